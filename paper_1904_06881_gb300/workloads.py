@@ -1,0 +1,171 @@
+"""Seeded synthetic inputs: solid masks, initial density/phase fields and
+parameter sets shaped like the tests of arXiv:1904.06881.
+
+This module holds geometry and random numbers only -- none of the method's
+arithmetic.  Both the CUDA library and the CPU oracle are fed from it.
+
+Physical parameters
+-------------------
+Free-energy parameters are Table 1, set 1 (lambda = 0.6, 1, 1; kappa = 0.01,
+1, 1; chi = 5), which gives the liquid-liquid profile tanh(x/2), i.e. an
+interface of width 4 (Sec. III, Eqs. liquidliquidalpha, profile).  The
+Carnahan-Starling constants are the printed a = 0.037, b = 0.2, R = 1
+(Sec. II.A).  The temperature is T = 0.8 T_c; the coexistence densities of
+that EOS are the numbers RHO_L, RHO_G below (liquid/gas ratio 14.1).  The
+step with the paper's pressure-form force and exact-difference forcing is
+not stable from a tanh initial state at lower temperatures (higher ratios)
+on these lattices, so every workload uses this temperature.
+
+Fields are numpy arrays shaped (nz, ny, nx) with x fastest; masks are uint8
+with 1 = solid.  Phases: C1 gas, C2 liquid with phi = +chi ("liquid 1"),
+C3 liquid with phi = -chi ("liquid 2", the lubricant).
+"""
+import numpy as np
+
+D2Q9, D3Q27 = 0, 1
+WET_FORCE, WET_GEOM_EXTRAP, WET_GEOM_INTERP = 0, 1, 2
+
+SET1 = dict(lam=(0.6, 1.0, 1.0), kappa=(0.01, 1.0, 1.0), chi=5.0)
+CS_EOS = dict(a=0.037, b=0.2, R=1.0)
+# Coexistence densities of the Carnahan-Starling EOS above at T = 0.8 T_c.
+RHO_L = 6.143914427184784
+RHO_G = 0.43446462473239633
+KINETIC = dict(beta=0.5, tau_g=1.0, Gamma=1.0)   # tau = 1 for f and g, nu = 1/6
+
+
+def base_params(**over):
+    p = dict(SET1)
+    p.update(CS_EOS)
+    p.update(KINETIC)
+    p.update(rho_l=RHO_L, rho_g=RHO_G, wetting=WET_FORCE, theta_deg=(90.0, 90.0, 90.0),
+             kw_rho=0.0, kw_phi=0.0)
+    p.update(over)
+    return p
+
+
+def phase_fields(C2, C3, rho_l=RHO_L, rho_g=RHO_G, chi=5.0):
+    """(rho, phi) from liquid concentrations: C1 = 1 - C2 - C3 (Eq. definitionCsum),
+    rho = rho_l + C1 (rho_g - rho_l) (Eq. definitionC1), phi = chi (C2 - C3)."""
+    C1 = 1.0 - C2 - C3
+    rho = rho_l + C1 * (rho_g - rho_l)
+    phi = chi * (C2 - C3)
+    return rho, phi
+
+
+def _blob(dist, R, width):
+    """Indicator of 'inside' with a tanh edge: 1 inside (dist < R), 0 outside."""
+    return 0.5 * (1.0 - np.tanh((dist - R) / width))
+
+
+def _noise(shape, seed, amp):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-amp, amp, shape), rng.uniform(-amp, amp, shape)
+
+
+def sessile_drop_2d(nx, ny, R, xc=None, yc=0.5, liquid=2, width=2.0, walls=("bottom", "top"),
+                    noise=0.0, seed=0, rho_l=RHO_L, rho_g=RHO_G, chi=5.0):
+    """2D drop of liquid C2 (liquid=2) or C3 (liquid=3) centred at (xc, yc) in
+    gas; solid rows y=0 (bottom) and y=ny-1 (top).  The wall plane of the
+    bottom wall lies at y = 0.5 (halfway bounce-back)."""
+    xc = nx / 2.0 if xc is None else xc
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    inside = _blob(np.hypot(x - xc, y - yc), R, width)
+    C2 = inside if liquid == 2 else np.zeros_like(inside)
+    C3 = inside if liquid == 3 else np.zeros_like(inside)
+    if noise:
+        n2, n3 = _noise(C2.shape, seed, noise)
+        C2, C3 = C2 + n2, C3 + n3
+    rho, phi = phase_fields(C2, C3, rho_l, rho_g, chi)
+    mask = np.zeros((ny, nx), np.uint8)
+    if "bottom" in walls:
+        mask[0, :] = 1
+    if "top" in walls:
+        mask[ny - 1, :] = 1
+    return mask[None], rho[None], phi[None]
+
+
+# ---------------------------------------------------------------------------
+# Named workloads
+# ---------------------------------------------------------------------------
+def c0_sessile_drop(seed=0):
+    """D2Q9 64x64, periodic in x, solid rows at y=0 and y=63; liquid-1 cap of
+    radius 16 on the bottom wall (centre (32, 0.5)) in gas; tanh edge of
+    width 4; force wetting with kappa^w = 0 (theta = 90 deg); +-1e-3 uniform
+    noise on C2 and C3; 1000 steps."""
+    mask, rho, phi = sessile_drop_2d(64, 64, 16.0, xc=32.0, yc=0.5, noise=1e-3, seed=seed)
+    return dict(name="c0_sessile_drop_d2q9_64x64", lattice=D2Q9, nx=64, ny=64, nz=1,
+                params=base_params(wetting=WET_FORCE), mask=mask, rho=rho, phi=phi, steps=1000)
+
+
+def c1_capillary(wetting=WET_GEOM_INTERP, nx=1024, ny=64, wall=12, x_in=256, x_out=960):
+    """D2Q9 1024x64 capillary filling: solid slabs y<12 and y>=52 for
+    x in [256, 960) leave a channel of height 40 between a liquid-1 reservoir
+    (x < 256, full height) and a gas reservoir (x >= 960).  Geometric wetting
+    with theta_21 = 30, theta_31 = 60, theta_23 = 120 deg.  50 000 steps."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    mask = np.zeros((ny, nx), np.uint8)
+    slab = (x >= x_in) & (x < x_out) & ((y < wall) | (y >= ny - wall))
+    mask[slab] = 1
+    # liquid slab x in [0, x_in) on the periodic ring, tanh edges of width 4
+    centre = 0.5 * (x_in - 1)
+    xp = np.mod(x - centre + nx / 2, nx) - nx / 2
+    C2 = _blob(np.abs(xp), 0.5 * x_in, 2.0)
+    C3 = np.zeros_like(C2)
+    rho, phi = phase_fields(C2, C3)
+    params = base_params(wetting=wetting, theta_deg=(30.0, 60.0, 120.0))
+    return dict(name="c1_capillary_d2q9_%dx%d" % (nx, ny), lattice=D2Q9, nx=nx, ny=ny, nz=1,
+                params=params, mask=mask[None], rho=rho[None], phi=phi[None], steps=50000,
+                channel=dict(x_in=x_in, x_out=x_out, wall=wall, H=ny - 2 * wall))
+
+
+def c2_lubricated(nx=192, ny=192, nz=128, R=32.0, lub=6, gap=4, kw_rho=0.0):
+    """D3Q27 192x192x128 lubricated substrate: solid planes z=0 and z=nz-1, a
+    liquid-2 (C3) lubricant film z in [1, lub], a liquid-1 (C2) sphere of
+    radius R whose bottom lies `gap` nodes above the film, gas elsewhere.
+    Force wetting.  10 000 steps."""
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    zc = lub + gap + R
+    C2 = _blob(np.sqrt((x - nx / 2) ** 2 + (y - ny / 2) ** 2 + (z - zc) ** 2), R, 2.0)
+    C3 = 0.5 * (1.0 - np.tanh((z - (lub + 0.5)) / 2.0)) * (1.0 - C2)
+    rho, phi = phase_fields(C2, C3)
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    mask[0] = 1
+    mask[nz - 1] = 1
+    params = base_params(wetting=WET_FORCE, theta_deg=(90.0, 20.0, 90.0), kw_rho=kw_rho)
+    return dict(name="c2_lubricated_d3q27_%dx%dx%d" % (nx, ny, nz), lattice=D3Q27, nx=nx, ny=ny,
+                nz=nz, params=params, mask=mask, rho=rho, phi=phi, steps=10000)
+
+
+def c3_sweep(seed=3, n=256, sizes=(64, 128, 256, 512)):
+    """Batched D2Q9 contact-angle sweep: n draws of L from `sizes`, a sessile
+    drop of radius L/4 on the bottom wall, theta_21 ~ U[30, 150] deg; each
+    draw runs with force and geometric-interpolation wetting (2n lattices).
+    5000 steps."""
+    rng = np.random.default_rng(seed)
+    Ls = rng.choice(sizes, size=n)
+    th = rng.uniform(30.0, 150.0, size=n)
+    out = []
+    for k in range(n):
+        L = int(Ls[k])
+        for wet in (WET_FORCE, WET_GEOM_INTERP):
+            out.append(dict(L=L, theta=float(th[k]), wetting=wet, seed=seed * 100003 + k))
+    return out
+
+
+def c3_lattice(item):
+    L = item["L"]
+    mask, rho, phi = sessile_drop_2d(L, L, L / 4.0, xc=L / 2.0, yc=0.5)
+    th = (item["theta"], item["theta"], 90.0)
+    params = base_params(wetting=item["wetting"], theta_deg=th)
+    return dict(name="c3_drop_%d" % L, lattice=D2Q9, nx=L, ny=L, nz=1, params=params,
+                mask=mask, rho=rho, phi=phi, steps=5000)
+
+
+def big_periodic_drop_2d(n=4096, R=None):
+    """Large D2Q9 periodic lattice with one liquid-1 drop (no walls)."""
+    R = n / 4.0 if R is None else R
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    C2 = _blob(np.hypot(x - n / 2, y - n / 2), R, 2.0)
+    rho, phi = phase_fields(C2, np.zeros_like(C2))
+    return dict(name="big_d2q9_%d" % n, lattice=D2Q9, nx=n, ny=n, nz=1, params=base_params(),
+                mask=np.zeros((1, n, n), np.uint8), rho=rho[None], phi=phi[None], steps=1000)
