@@ -1,0 +1,282 @@
+"""Benchmark of the ternary ELBM step on GB300.
+
+Workload: the D2Q9 1024x64 capillary-filling channel (geometric-interpolation
+wetting, angles 30/60/120 deg).  One benchmark step = one full time step of
+the lattice (moments, ghost layer, stencils, force, ELBM + LBGK collision,
+streaming with bounce-back).  The lattice state (9.4 MB) fits in L2, so a
+256 MB buffer is written between timed steps and each step is timed on its
+own with CUDA events on the lattice's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs one replica (weak scaling, no collective on
+the data path); rank 0 prints one JSON line with the max time over ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    from paper_1904_06881_gb300 import workloads as W
+
+    return W.c1_capillary()
+
+
+def algorithmic_bytes(Q, N):
+    """Per launch of the fused step kernel: read f, g (Q floats each), write
+    f, g, read rho, phi (2 floats) and the node flag (1 byte) per node."""
+    return N * (16 * Q + 9)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1904_06881_gb300 import tlb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    wl = workload()
+    stream = torch.cuda.Stream()
+    lat = tlb.lattice_from_workload(wl)
+    tlb.tlb_set_stream(lat.h, stream.cuda_stream)
+    N, Q = lat.N, lat.Q
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one_step():
+        for ph in (0, 1, 2):
+            tlb.tlb_step_phase(lat.h, ph)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            flush.fill_(1.0)
+            one_step()
+        stream.synchronize()
+        tlb.tlb_sync(lat.h)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        launches0 = lat.launches
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                tlb.tlb_step_phase(lat.h, 0)
+                tlb.tlb_step_phase(lat.h, 1)
+                ev[k][1].record(stream)
+                tlb.tlb_step_phase(lat.h, 2)
+                ev[k][2].record(stream)
+            stream.synchronize()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        launches = lat.launches - launches0
+        tlb.tlb_sync(lat.h)
+    step_ms = sum(e[0].elapsed_time(e[2]) for e in ev)
+    kern_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    ms_per_step = step_ms / args.steps
+    value = world * N / (ms_per_step * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: init from host, steps, fields to host
+    e2e = None
+    if rank == 0:
+        e2e = e2e_run(wl, tlb)
+    peak, peak_kind = hbm_peak()
+    achieved = algorithmic_bytes(Q, N) / (kern_ms * 1e-3) / 1e9
+    result = {
+        "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["name"], "lattice": "D2Q9", "nx": wl["nx"], "ny": wl["ny"],
+                   "wetting": "geometric interpolation", "angles_deg": [30, 60, 120],
+                   "density_ratio": 14.14, "l2": "256 MB buffer written between timed steps; each step timed alone",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "step_kernel<D2Q9> (fused stencil/collision/stream)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind + " (hbm_gbs)",
+                     "traffic": None, "kernel_ms": round(kern_ms, 5),
+                     "algorithmic_bytes_per_launch": algorithmic_bytes(Q, N)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "host_wall_s": round(wall, 4),
+    }
+    if e2e:
+        result["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return result if rank == 0 else None
+
+
+def e2e_run(wl, tlb, nsteps=1000, reps=3):
+    """MLUPS of whole jobs through the public C ABI: tlb_init_fields from host
+    arrays, nsteps steps, tlb_get_fields back to host arrays."""
+    lat = tlb.Lattice(wl["lattice"], wl["nx"], wl["ny"], wl["nz"], **wl["params"])
+    lat.set_solid(wl["mask"])
+    rho = np.ascontiguousarray(wl["rho"], dtype=np.float64)
+    phi = np.ascontiguousarray(wl["phi"], dtype=np.float64)
+    lat.init_fields(rho, phi)
+    lat.step(10)
+    lat.fields()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        lat.init_fields(rho, phi)
+        lat.step(nsteps)
+        f = lat.fields()
+        times.append(time.perf_counter() - t0)
+        assert np.isfinite(f["rho"]).all()
+    t = min(times)
+    N = lat.N
+    h2d = 2 * N * 8
+    d2h = (2 + lat.D + 3) * N * 8
+    return {"value": round(N * nsteps / t / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d / nsteps, 1),
+            "d2h_bytes_per_step": round(d2h / nsteps, 1),
+            "job": "tlb_init_fields (host FP64) + %d steps + tlb_get_fields (host FP64)" % nsteps}
+
+
+def cpu_baseline(wl, seconds=15.0):
+    """The FP64 oracle as it stands, on this host's cores, on the same
+    workload for as many steps as fit in about `seconds`."""
+    import oracle
+
+    o = oracle.from_workload(wl)
+    o.step(1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(5)
+        n += 5
+    dt = time.perf_counter() - t0
+    N = wl["nx"] * wl["ny"] * wl["nz"]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    return {"value": round(N * n / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d full time steps of %s (%d nodes) in %.1f s" % (n, wl["name"], N, dt)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    wl = workload()
+    import oracle
+
+    o = oracle.from_workload(wl)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    N = wl["nx"] * wl["ny"] * wl["nz"]
+    value = N * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    return {"impl": "reference", "metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "lattice": "D2Q9", "nx": wl["nx"], "ny": wl["ny"]},
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": "%d full time steps of %s on the host cores" % (args.steps, wl["name"])},
+            "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

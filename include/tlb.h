@@ -1,0 +1,209 @@
+/*
+ * tlb.h -- C ABI of the GB300 (sm_103a) ternary free-energy lattice Boltzmann
+ * library: one fused time step of the model of Bala, Pepona, Karlin,
+ * Kusumaatmaja & Semprebon, "Wetting boundaries for a ternary high density
+ * ratio lattice Boltzmann method" (arXiv:1904.06881), Sec. II-IV.
+ *
+ * Every entry point returns an int: TLB_OK (0) or a negative TLB_E_* code;
+ * tlb_strerror() names it and tlb_last_error_message() gives the detail of
+ * the last failure on the calling thread.  Pointers marked (host) are read or
+ * written synchronously and not retained; pointers marked (device) must be
+ * device memory of the context's GPU.  Contexts and servers are owned by the
+ * library and freed only by tlb_destroy / tlb_server_destroy.  A context may
+ * be used from one host thread at a time.
+ *
+ * Layout: a lattice has N = nx*ny*nz nodes, node n = x + nx*(y + ny*z),
+ * x fastest; every axis is periodic and walls come from the solid mask.
+ * Vector fields are component-major (u[a*N + n]).  D2Q9 lattices have nz = 1.
+ * Phases: C1 gas; C2 liquid with phi = +chi; C3 liquid with phi = -chi
+ * (Sec. II.A, Eqs. definitionC1-C3).
+ */
+#ifndef TLB_H
+#define TLB_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define TLB_OK              0
+#define TLB_E_INVAL        -1   /* bad argument, size or parameter */
+#define TLB_E_NOMEM        -2   /* device or host allocation failed */
+#define TLB_E_CUDA         -3   /* a CUDA runtime call failed */
+#define TLB_E_UNSUPPORTED  -4   /* valid request this library does not implement */
+#define TLB_E_UNCALIBRATED -5   /* force wetting with angles != 90 deg and no kappa^w */
+#define TLB_E_DIVERGED     -6   /* a non-positive density or population was met */
+#define TLB_E_TIMEOUT      -7   /* a bounded device wait gave up */
+#define TLB_E_BUSY         -8   /* no capacity (server queue or memory budget) */
+#define TLB_E_NOTFOUND     -9   /* unknown ticket */
+
+enum { TLB_D2Q9 = 0, TLB_D3Q27 = 1 };
+enum { TLB_WET_FORCE = 0, TLB_WET_GEOM_EXTRAP = 1, TLB_WET_GEOM_INTERP = 2 };
+
+/* Full parameter set.  tlb_params_default() fills Table 1 set 1 (lambda =
+ * 0.6, 1, 1; kappa = 0.01, 1, 1), chi = 5, the printed Carnahan-Starling
+ * constants a = 0.037, b = 0.2, R = 1 (Sec. II.A), tau = 1 for f and g
+ * (beta = 0.5, nu = 1/6; Sec. II.C), Gamma = 1 and coexistence densities at
+ * T = 0.8 T_c.  All values are FP64 on the host. */
+typedef struct {
+    int    lattice;              /* TLB_D2Q9 or TLB_D3Q27 */
+    int    nx, ny, nz;
+    double lambda[3], kappa[3];  /* Eqs. BulkEnergy, InterfEnergy */
+    double chi;
+    double a, b, R;              /* EOS constants before rescaling (Eq. PsiEOS) */
+    double rho_l, rho_g;         /* coexistence densities to reach, rho_l > rho_g > 0 */
+    double beta;                 /* ELBM beta; nu = (1/beta - 1)/6 */
+    double tau_g;                /* LBGK relaxation time of g (Eq. CahnHilliardLBM) */
+    double Gamma;                /* mobility constant of g^eq */
+    int    wetting;              /* TLB_WET_* (Sec. IV.A-B) */
+    double theta_deg[3];         /* theta_21, theta_31, theta_23 (Sec. IV.A convention) */
+    double kw_rho, kw_phi;       /* force-method strengths (Eq. forceBC) */
+    int    g_fp16;               /* 1: store g as FP16 scaled by 1/chi (reduced precision) */
+} tlb_params;
+
+/* Constants derived at creation (host FP64). */
+typedef struct {
+    double T, a, b, R;           /* temperature; a, b after rescaling */
+    double rho_l, rho_g;         /* coexistence densities actually used */
+    double C, Psi0;              /* constants of Eq. PsiEOS */
+    double Tc;                   /* critical temperature of the EOS */
+    double kappa_rr, kappa_pp, kappa_rp;   /* gradient coefficients (Sec. II.B) */
+} tlb_derived;
+
+typedef struct tlb_ctx tlb_ctx;
+
+const char *tlb_strerror(int code);
+const char *tlb_last_error_message(void);
+/* Library version and the compute capability the kernels were built for. */
+int tlb_version(int *major, int *minor, int *sm);
+
+/* Device allocator used for every later allocation (NULL restores
+ * cudaMalloc/cudaFree).  alloc(bytes, user) returns device memory or NULL;
+ * free_(ptr, user) releases it. */
+int tlb_set_allocator(void *(*alloc)(size_t bytes, void *user), void (*free_)(void *ptr, void *user),
+                      void *user);
+
+int tlb_params_default(tlb_params *p);
+
+/* Create a lattice (Sec. II).  densities = {rho_liquid, rho_gas} (both
+ * liquids share rho_l, Sec. II.A); kappas = {kappa1, kappa2, kappa3} with
+ * lambdas of Table 1 set 1; viscosities = kinematic viscosity of the three
+ * phases, which must be equal (one beta, Sec. II.C) else TLB_E_UNSUPPORTED;
+ * angles_deg = {theta_21, theta_31, theta_23}.  The density ratio fixes the
+ * temperature of the Carnahan-Starling EOS; a and b are scaled so that the
+ * coexistence densities are the ones given.  Force wetting with any angle
+ * other than 90 deg needs explicit strengths (tlb_create_ex): it returns
+ * TLB_E_UNCALIBRATED here. */
+int tlb_create(int lattice, int nx, int ny, int nz, const double densities[2], const double kappas[3],
+               const double viscosities[3], int wetting, const double angles_deg[3], tlb_ctx **out);
+int tlb_create_ex(const tlb_params *p, tlb_ctx **out);
+void tlb_destroy(tlb_ctx *ctx);
+int tlb_get_params(const tlb_ctx *ctx, tlb_params *out);
+int tlb_get_derived(const tlb_ctx *ctx, tlb_derived *out);
+
+/* Work stream of the context (cudaStream_t); NULL is the legacy default
+ * stream.  tlb_step and the *_device calls are asynchronous on it. */
+int tlb_set_stream(tlb_ctx *ctx, void *cuda_stream);
+
+/* Solid mask (host, N bytes, 1 = solid).  Resets the ghost-node list and the
+ * wall flags used by the wall rules of Sec. IV. */
+int tlb_set_solid(tlb_ctx *ctx, const uint8_t *mask);
+
+/* Initial fields (host FP64): rho, phi (N each), u = fluid velocity (D*N) or
+ * NULL for rest.  f = f^eq(rho, u - F/(2 rho)) and g = g^eq(phi, u, mu_phi)
+ * with F and mu_phi of the initial fields (Sec. II.C). Synchronous. */
+int tlb_init_fields(tlb_ctx *ctx, const double *rho, const double *phi, const double *u);
+/* Same with device FP32 inputs; asynchronous on the context stream. */
+int tlb_init_fields_device(tlb_ctx *ctx, const float *rho, const float *phi, const float *u);
+
+/* Advance nsteps time steps (Eqs. ELBMequation, CahnHilliardLBM with the
+ * wall rules and wetting scheme of Sec. IV).  Asynchronous; returns the
+ * sticky error status seen by the last synchronising call. */
+int tlb_step(tlb_ctx *ctx, int nsteps);
+/* One phase of a time step, for per-kernel timing: phase 0 computes the
+ * moments rho, phi; 1 fills the ghost layer; 2 runs the fused stencil /
+ * collision / streaming kernel and completes the step.  Issuing 0, 1, 2 in
+ * order is exactly one tlb_step.  Asynchronous. */
+int tlb_step_phase(tlb_ctx *ctx, int phase);
+/* Wait for the context stream and report TLB_E_DIVERGED if a kernel flagged
+ * a non-positive density or population since the last check. */
+int tlb_sync(tlb_ctx *ctx);
+
+/* Fields of the current state (host FP64; any pointer may be NULL): rho,
+ * phi (N), bare velocity u = sum f c / rho (D*N), concentrations C (3*N,
+ * Eqs. definitionC1-C3).  Solid nodes read 0.  Synchronous. */
+int tlb_get_fields(tlb_ctx *ctx, double *rho, double *phi, double *u, double *C);
+/* Device FP32 outputs (rho, phi: N; u: D*N; any may be NULL); asynchronous. */
+int tlb_get_fields_device(tlb_ctx *ctx, float *rho, float *phi, float *u);
+
+/* FP64 sums over fluid nodes: out = {sum rho, sum phi, sum C1, sum C2,
+ * sum C3, 0.5 sum rho |u|^2}.  Synchronous. */
+int tlb_diagnostics(tlb_ctx *ctx, double out[6]);
+
+/* Auxiliary fields recomputed from the current state, as FP64 on the host:
+ * which = 0 p0, 1 mu_rho, 2 mu_phi, 3..5 F (total force incl. wetting force),
+ * 6..11 P_xx,P_yy,P_zz,P_xy,P_xz,P_yz, 12 rho incl. ghost layer, 13 phi incl.
+ * ghost layer.  Solid nodes read 0 for which < 12. */
+int tlb_get_aux(tlb_ctx *ctx, int which, double *out);
+
+/* Pre-collision populations (host FP64, Q*N each, f[i*N + n]); the lattice
+ * direction order is that of tlb_lattice_directions.  Synchronous. */
+int tlb_get_populations(tlb_ctx *ctx, double *f, double *g);
+int tlb_set_populations(tlb_ctx *ctx, const double *f, const double *g);
+/* Lattice directions: c (Q*3 ints) and weights w (Q doubles); returns Q. */
+int tlb_lattice_directions(int lattice, int *c, double *w);
+
+/* Checkpoint: the populations and step counter in an opaque host buffer. */
+size_t tlb_snapshot_bytes(const tlb_ctx *ctx);
+int tlb_snapshot(tlb_ctx *ctx, void *host, size_t bytes);
+int tlb_restore(tlb_ctx *ctx, const void *host, size_t bytes);
+long long tlb_steps_done(const tlb_ctx *ctx);
+/* Device bytes held by the context. */
+size_t tlb_device_bytes(const tlb_ctx *ctx);
+/* Kernel launches issued by the context since creation. */
+long long tlb_launch_count(const tlb_ctx *ctx);
+
+/* ---- batched lattices: many contexts advanced by one launch per phase ---- */
+/* Advance every context in ctxs[0..n) by nsteps, with one launch per kernel
+ * phase covering all lattices (a tile -> lattice table).  All contexts must
+ * share the lattice type and the stream of ctxs[0]. */
+int tlb_step_batch(tlb_ctx *const *ctxs, int n, int nsteps);
+
+/* ---- request server (continuous batching) ---- */
+typedef struct tlb_server tlb_server;
+typedef struct {
+    tlb_params params;           /* lattice, sizes and physics */
+    const uint8_t *mask;         /* host, N bytes (may be NULL: no walls) */
+    const double *rho, *phi;     /* host initial fields, N each */
+    int nsteps;                  /* steps to run */
+} tlb_request;
+typedef struct {
+    int state;                   /* TLB_REQ_* */
+    int status;                  /* TLB_OK or the error that failed it */
+    double submit_s, start_s, done_s;   /* host wall-clock seconds */
+    double mass[6];              /* tlb_diagnostics at completion */
+} tlb_result;
+enum { TLB_REQ_QUEUED = 0, TLB_REQ_RUNNING = 1, TLB_REQ_DONE = 2, TLB_REQ_FAILED = 3 };
+
+/* Server with a device-memory budget for resident lattices and a cap on
+ * lattices advanced together; steps_per_round steps run between admissions. */
+int tlb_server_create(size_t hbm_budget_bytes, int max_active, int steps_per_round, void *cuda_stream,
+                      tlb_server **out);
+/* Copy a request in; returns a ticket.  TLB_E_INVAL if the request can never
+ * fit the budget. */
+int tlb_submit(tlb_server *s, const tlb_request *req, uint64_t *ticket);
+/* Advance the server by one round (admit, step all active lattices together,
+ * retire finished ones).  Returns the number of active lattices or < 0. */
+int tlb_server_pump(tlb_server *s);
+/* State of a ticket; when DONE, rho/phi (host, N each, may be NULL) receive
+ * the final fields and the ticket is released. */
+int tlb_poll(tlb_server *s, uint64_t ticket, tlb_result *res, double *rho, double *phi);
+int tlb_server_stats(tlb_server *s, int *queued, int *active, size_t *bytes_in_use);
+void tlb_server_destroy(tlb_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

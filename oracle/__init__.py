@@ -253,3 +253,16 @@ class Oracle:
     @property
     def alpha_clipped(self):
         return lib().tlbo_alpha_clipped(self._h)
+
+
+def from_workload(wl, **over):
+    """Oracle lattice with the mask and initial fields of a workloads.* dict."""
+    p = dict(wl["params"])
+    p.update(over)
+    o = Oracle(lattice=wl["lattice"], nx=wl["nx"], ny=wl["ny"], nz=wl["nz"], lam=p["lam"], kappa=p["kappa"],
+               chi=p["chi"], a=p["a"], b=p["b"], R=p["R"], rho_l=p["rho_l"], rho_g=p["rho_g"], beta=p["beta"],
+               tau_g=p["tau_g"], Gamma=p["Gamma"], wetting=p["wetting"], theta_deg=p["theta_deg"],
+               kw_rho=p["kw_rho"], kw_phi=p["kw_phi"])
+    o.set_solid(wl["mask"])
+    o.init_fields(wl["rho"], wl["phi"])
+    return o

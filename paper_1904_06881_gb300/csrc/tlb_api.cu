@@ -1,0 +1,1176 @@
+// tlb_api.cu -- host side of the C ABI declared in include/tlb.h: parameter
+// derivation (Carnahan-Starling coexistence, Sec. II.A), mask preprocessing
+// (ghost layer, wall flags, Sec. IV), buffers, kernel launches, batched
+// stepping and the request server.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tlb.h"
+#include "tlb_device.cuh"
+#include "tlb_internal.h"
+
+namespace tlb {
+template <int D>
+void ghosts_batch_launch(const BatchEntry *entries, const int2 *gl, int n, cudaStream_t st);
+}
+
+using namespace tlb;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_errmsg;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_errmsg = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(TLB_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+extern "C" const char *tlb_strerror(int code)
+{
+    switch (code) {
+    case TLB_OK: return "ok";
+    case TLB_E_INVAL: return "invalid argument";
+    case TLB_E_NOMEM: return "out of memory";
+    case TLB_E_CUDA: return "CUDA error";
+    case TLB_E_UNSUPPORTED: return "unsupported";
+    case TLB_E_UNCALIBRATED: return "force wetting needs kappa^w for angles other than 90 deg";
+    case TLB_E_DIVERGED: return "non-positive density or population";
+    case TLB_E_TIMEOUT: return "device wait timed out";
+    case TLB_E_BUSY: return "busy";
+    case TLB_E_NOTFOUND: return "unknown ticket";
+    default: return "unknown error";
+    }
+}
+
+extern "C" const char *tlb_last_error_message(void) { return g_errmsg.c_str(); }
+
+extern "C" int tlb_version(int *major, int *minor, int *sm)
+{
+    if (major) *major = 1;
+    if (minor) *minor = 0;
+    if (sm) *sm = 103;
+    return TLB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// allocator hook
+// ---------------------------------------------------------------------------
+static void *(*g_alloc)(size_t, void *) = nullptr;
+static void (*g_free)(void *, void *) = nullptr;
+static void *g_alloc_user = nullptr;
+
+extern "C" int tlb_set_allocator(void *(*alloc)(size_t, void *), void (*free_)(void *, void *), void *user)
+{
+    if ((alloc == nullptr) != (free_ == nullptr)) return fail(TLB_E_INVAL, "allocator and free must both be set");
+    g_alloc = alloc;
+    g_free = free_;
+    g_alloc_user = user;
+    return TLB_OK;
+}
+
+struct Block {
+    void *ptr;
+    bool hooked;
+    void *user;
+    void (*fr)(void *, void *);
+};
+
+static int dev_alloc(std::vector<Block> &owned, void **out, size_t bytes, size_t *counter)
+{
+    void *p = nullptr;
+    bytes = std::max<size_t>(bytes, 256);
+    if (g_alloc) {
+        p = g_alloc(bytes, g_alloc_user);
+        if (!p) return fail(TLB_E_NOMEM, "allocator returned NULL for %zu bytes", bytes);
+        owned.push_back({p, true, g_alloc_user, g_free});
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return fail(TLB_E_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        owned.push_back({p, false, nullptr, nullptr});
+    }
+    if (counter) *counter += bytes;
+    *out = p;
+    return TLB_OK;
+}
+
+static void dev_free_all(std::vector<Block> &owned)
+{
+    for (auto &b : owned) {
+        if (b.hooked) b.fr(b.ptr, b.user);
+        else cudaFree(b.ptr);
+    }
+    owned.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Carnahan-Starling EOS (Sec. II.A), host FP64.  Coexistence from the
+// textbook CS pressure and chemical potential; C and Psi0 from the printed
+// Psi_eos and its derivative.
+// ---------------------------------------------------------------------------
+namespace {
+struct CS {
+    double a, b, R, T;
+    double p(double r) const
+    {
+        double e = b * r / 4.0;
+        return r * R * T * (1 + e + e * e - e * e * e) / std::pow(1 - e, 3) - a * r * r;
+    }
+    double mu(double r) const
+    {
+        double e = b * r / 4.0;
+        return R * T * (std::log(r) + (8 * e - 9 * e * e + 3 * e * e * e) / std::pow(1 - e, 3)) - 2 * a * r;
+    }
+    double dp(double r) const
+    {
+        double e = b * r / 4.0, om = 1 - e;
+        double Z = (1 + e + e * e - e * e * e) / (om * om * om);
+        double dZ = ((1 + 2 * e - 3 * e * e) * om + 3 * (1 + e + e * e - e * e * e)) / (om * om * om * om);
+        return R * T * (Z + e * dZ) - 2 * a * r;
+    }
+    double psi_printed(double r, double C) const
+    {
+        double br = b * r;
+        return r * (C - a * r - 8 * R * T * (br - 6) / ((br - 4) * (br - 4)) + R * T * std::log(r));
+    }
+    double dpsi_printed(double r, double C) const
+    {
+        double br = b * r, q = br - 4;
+        return C - 2 * a * r + R * T * (1 + std::log(r)) + 16 * R * T * (br - 12) / (q * q * q);
+    }
+    // unstable interval [s1, s2] where dp/drho < 0
+    bool spinodal(double &s1, double &s2) const
+    {
+        const int M = 6000;
+        double top = 4.0 / b;
+        int k1 = -1, k2 = -1;
+        for (int k = 1; k < M; ++k)
+            if (dp(top * k / M) < 0) {
+                if (k1 < 0) k1 = k;
+                k2 = k;
+            }
+        if (k1 < 0) return false;
+        double lo = top * (k1 - 1) / M, hi = top * k1 / M;
+        for (int it = 0; it < 120; ++it) {
+            double m = 0.5 * (lo + hi);
+            (dp(m) < 0 ? hi : lo) = m;
+        }
+        s1 = hi;
+        lo = top * k2 / M;
+        hi = top * (k2 + 1) / M;
+        for (int it = 0; it < 120; ++it) {
+            double m = 0.5 * (lo + hi);
+            (dp(m) < 0 ? lo : hi) = m;
+        }
+        s2 = lo;
+        return true;
+    }
+    // coexistence by a search over ln(rho_g): the liquid root of p(rho_l) = p(rho_g)
+    // beyond the spinodal, then mu(rho_l) = mu(rho_g)
+    bool coexist(double &rg, double &rl) const
+    {
+        double s1, s2;
+        if (!spinodal(s1, s2)) return false;
+        double pmin = p(s2), pmax = p(s1);
+        auto liquid_for = [&](double pg) {
+            double lo = s2, hi = 4.0 / b * (1 - 1e-14);
+            for (int it = 0; it < 200; ++it) {
+                double m = 0.5 * (lo + hi);
+                (p(m) < pg ? lo : hi) = m;
+            }
+            return 0.5 * (lo + hi);
+        };
+        // admissible gas densities: p(rho_g) in (max(pmin, 0), pmax)
+        double lgl = std::log(1e-300), lgh = std::log(s1);
+        // lower end: the smallest rho_g with p(rho_g) > pmin
+        if (pmin > 0) {
+            double lo = lgl, hi = lgh;
+            for (int it = 0; it < 200; ++it) {
+                double m = 0.5 * (lo + hi);
+                (p(std::exp(m)) < pmin ? lo : hi) = m;
+            }
+            lgl = hi;
+        }
+        auto G = [&](double lg) {
+            double r = std::exp(lg);
+            return mu(liquid_for(p(r))) - mu(r);
+        };
+        double glo = G(lgl);
+        for (int it = 0; it < 200; ++it) {
+            double m = 0.5 * (lgl + lgh);
+            double gm = G(m);
+            if ((gm < 0) == (glo < 0)) { lgl = m; glo = gm; } else lgh = m;
+            if (lgh - lgl < 1e-15) break;
+        }
+        rg = std::exp(0.5 * (lgl + lgh));
+        rl = liquid_for(p(rg));
+        return true;
+    }
+};
+
+double critical_T(double a, double b, double R)
+{
+    double lo = 0.01 * a / (b * R), hi = a / (b * R);
+    for (int it = 0; it < 80; ++it) {
+        double m = 0.5 * (lo + hi);
+        double s1, s2;
+        CS e{a, b, R, m};
+        (e.spinodal(s1, s2) ? lo : hi) = m;
+    }
+    return 0.5 * (lo + hi);
+}
+}  // namespace
+
+extern "C" int tlb_params_default(tlb_params *p)
+{
+    if (!p) return fail(TLB_E_INVAL, "null params");
+    std::memset(p, 0, sizeof(*p));
+    p->lattice = TLB_D2Q9;
+    p->nx = p->ny = 64;
+    p->nz = 1;
+    p->lambda[0] = 0.6; p->lambda[1] = 1.0; p->lambda[2] = 1.0;
+    p->kappa[0] = 0.01; p->kappa[1] = 1.0; p->kappa[2] = 1.0;
+    p->chi = 5.0;
+    p->a = 0.037; p->b = 0.2; p->R = 1.0;
+    p->rho_l = 6.143914427184784;
+    p->rho_g = 0.43446462473239633;
+    p->beta = 0.5;
+    p->tau_g = 1.0;
+    p->Gamma = 1.0;
+    p->wetting = TLB_WET_FORCE;
+    p->theta_deg[0] = p->theta_deg[1] = p->theta_deg[2] = 90.0;
+    return TLB_OK;
+}
+
+static int derive(const tlb_params &p, tlb_derived &d)
+{
+    if (!(p.rho_l > p.rho_g && p.rho_g > 0)) return fail(TLB_E_INVAL, "need rho_l > rho_g > 0");
+    if (!(p.a > 0 && p.b > 0 && p.R > 0)) return fail(TLB_E_INVAL, "EOS constants must be positive");
+    double Tc = critical_T(p.a, p.b, p.R);
+    double ratio = p.rho_l / p.rho_g;
+    // the density ratio fixes T; bisection on T/T_c
+    double lo = 0.02, hi = 0.9999, rg = 0, rl = 0;
+    for (int it = 0; it < 64; ++it) {
+        double m = 0.5 * (lo + hi);
+        CS e{p.a, p.b, p.R, m * Tc};
+        if (!e.coexist(rg, rl)) { hi = m; continue; }
+        (rl / rg > ratio ? lo : hi) = m;
+    }
+    double T = 0.5 * (lo + hi) * Tc;
+    CS e0{p.a, p.b, p.R, T};
+    if (!e0.coexist(rg, rl)) return fail(TLB_E_INVAL, "no coexistence for density ratio %g", ratio);
+    // scaling a, b by s keeps T_c and the ratio and divides the densities by s
+    double s = rl / p.rho_l;
+    CS e{p.a * s, p.b * s, p.R, T};
+    if (!e.coexist(rg, rl)) return fail(TLB_E_INVAL, "no coexistence after rescaling");
+    d.T = T;
+    d.a = e.a;
+    d.b = e.b;
+    d.R = p.R;
+    d.Tc = Tc;
+    d.rho_g = rg;
+    d.rho_l = rl;
+    d.C = -e.dpsi_printed(rl, 0.0);
+    d.Psi0 = e.psi_printed(rl, d.C);
+    double drho = rl - rg;
+    d.kappa_rr = p.kappa[0] + (p.kappa[1] + p.kappa[2]) / (4 * drho * drho);
+    d.kappa_pp = (p.kappa[1] + p.kappa[2]) / (4 * p.chi * p.chi);
+    d.kappa_rp = (p.kappa[1] - p.kappa[2]) / (4 * p.chi * drho);
+    return TLB_OK;
+}
+
+static DevParams make_dev(const tlb_params &p, const tlb_derived &d)
+{
+    DevParams q;
+    std::memset(&q, 0, sizeof(q));
+    q.nx = p.nx;
+    q.ny = p.ny;
+    q.nz = p.nz;
+    q.N = (long long)p.nx * p.ny * p.nz;
+    q.lam1 = (float)p.lambda[0];
+    q.lam2 = (float)p.lambda[1];
+    q.lam3 = (float)p.lambda[2];
+    q.chi = (float)p.chi;
+    q.inv_chi = (float)(1.0 / p.chi);
+    q.a = (float)d.a;
+    q.b = (float)d.b;
+    q.RT = (float)(d.R * d.T);
+    q.C = (float)d.C;
+    q.Psi0 = (float)d.Psi0;
+    q.rho_l = (float)d.rho_l;
+    q.rho_g = (float)d.rho_g;
+    q.inv_drho = (float)(1.0 / (d.rho_l - d.rho_g));
+    q.inv_rgl = (float)(1.0 / (d.rho_g - d.rho_l));
+    q.krr = (float)d.kappa_rr;
+    q.kpp = (float)d.kappa_pp;
+    q.krp = (float)d.kappa_rp;
+    q.beta = (float)p.beta;
+    q.inv_tau_g = (float)(1.0 / p.tau_g);
+    q.Gamma = (float)p.Gamma;
+    q.wetting = p.wetting;
+    for (int k = 0; k < 3; ++k) q.cot[k] = (float)(1.0 / std::tan(p.theta_deg[k] * M_PI / 180.0));
+    q.kw_rho = (float)p.kw_rho;
+    q.kw_phi = (float)p.kw_phi;
+    q.g_fp16 = p.g_fp16;
+    q.g_scale = p.g_fp16 ? (float)(1.0 / p.chi) : 1.0f;
+    q.g_unscale = p.g_fp16 ? (float)p.chi : 1.0f;
+    return q;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct tlb_ctx {
+    tlb_params p;
+    tlb_derived d;
+    DevParams dp;
+    DevState s;
+    int D, Q;
+    long long N;
+    cudaStream_t stream = nullptr;
+    std::vector<Block> owned;
+    size_t bytes = 0;
+    std::vector<uint8_t> type_host;
+    std::vector<int> ghost_host;
+    int *ghosts_dev = nullptr;
+    size_t ghosts_cap = 0;
+    double *diag_part = nullptr, *diag_out = nullptr;
+    int diag_nb = 0;
+    long long steps = 0;
+    long long launches = 0;
+    int sticky = TLB_OK;
+};
+
+static int Qof(int lattice) { return lattice == TLB_D3Q27 ? 27 : 9; }
+static int Dof(int lattice) { return lattice == TLB_D3Q27 ? 3 : 2; }
+
+#define DISPATCH(ctx, call)                       \
+    do {                                          \
+        if ((ctx)->D == 2) Launch<2>::call;       \
+        else Launch<3>::call;                     \
+    } while (0)
+
+static int check_launch(tlb_ctx *c, int nlaunch)
+{
+    c->launches += nlaunch;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TLB_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return TLB_OK;
+}
+
+static int validate(const tlb_params &p)
+{
+    if (p.lattice != TLB_D2Q9 && p.lattice != TLB_D3Q27) return fail(TLB_E_INVAL, "lattice must be D2Q9 or D3Q27");
+    if (p.nx < 3 || p.ny < 3 || p.nz < 1) return fail(TLB_E_INVAL, "lattice too small (%d x %d x %d)", p.nx, p.ny, p.nz);
+    if (p.lattice == TLB_D2Q9 && p.nz != 1) return fail(TLB_E_INVAL, "D2Q9 needs nz = 1");
+    if (p.lattice == TLB_D3Q27 && p.nz < 3) return fail(TLB_E_INVAL, "D3Q27 needs nz >= 3");
+    if ((long long)p.nx * p.ny * p.nz > (1LL << 31) - 1) return fail(TLB_E_INVAL, "more than 2^31-1 nodes");
+    if (!(p.beta > 0 && p.beta <= 1)) return fail(TLB_E_INVAL, "beta must lie in (0, 1]");
+    if (!(p.tau_g >= 0.5)) return fail(TLB_E_INVAL, "tau_g must be >= 0.5");
+    if (!(p.chi > 0)) return fail(TLB_E_INVAL, "chi must be positive");
+    if (p.wetting < 0 || p.wetting > 2) return fail(TLB_E_INVAL, "unknown wetting scheme");
+    for (int k = 0; k < 3; ++k) {
+        double t = p.theta_deg[k];
+        if (p.wetting != TLB_WET_FORCE && !(t >= 20.0 && t <= 160.0))
+            return fail(TLB_E_UNSUPPORTED, "geometric wetting supports angles in [20, 160] deg (got %g)", t);
+        if (!(t > 0 && t < 180)) return fail(TLB_E_INVAL, "angle out of (0, 180)");
+    }
+    return TLB_OK;
+}
+
+extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
+{
+    if (!pin || !out) return fail(TLB_E_INVAL, "null argument");
+    *out = nullptr;
+    int rc = validate(*pin);
+    if (rc) return rc;
+    tlb_ctx *c = new tlb_ctx();
+    c->p = *pin;
+    rc = derive(c->p, c->d);
+    if (rc) { delete c; return rc; }
+    c->dp = make_dev(c->p, c->d);
+    c->D = Dof(c->p.lattice);
+    c->Q = Qof(c->p.lattice);
+    c->N = c->dp.N;
+    size_t N = (size_t)c->N, Q = (size_t)c->Q;
+    size_t gsz = c->p.g_fp16 ? 2 : 4;
+    void *ptr;
+#define ALLOC(field, nbytes)                                             \
+    do {                                                                 \
+        rc = dev_alloc(c->owned, &ptr, (nbytes), &c->bytes);             \
+        if (rc) { dev_free_all(c->owned); delete c; return rc; }         \
+        field = (decltype(field))ptr;                                    \
+    } while (0)
+    ALLOC(c->s.f[0], Q * N * 4);
+    ALLOC(c->s.f[1], Q * N * 4);
+    ALLOC(c->s.g[0], Q * N * gsz);
+    ALLOC(c->s.g[1], Q * N * gsz);
+    ALLOC(c->s.rho, N * 4);
+    ALLOC(c->s.phi, N * 4);
+    ALLOC(c->s.type, N);
+    ALLOC(c->s.status, 256);
+    c->diag_nb = c->D == 2 ? Launch<2>::diag_blocks(c->dp) : Launch<3>::diag_blocks(c->dp);
+    ALLOC(c->diag_part, (size_t)c->diag_nb * 6 * 8);
+    ALLOC(c->diag_out, 6 * 8);
+#undef ALLOC
+    c->s.cur = 0;
+    c->s.ghosts = nullptr;
+    c->s.nghost = 0;
+    cudaMemsetAsync(c->s.type, 0, N, c->stream);
+    cudaMemsetAsync(c->s.status, 0, 256, c->stream);
+    cudaMemsetAsync(c->s.f[0], 0, Q * N * 4, c->stream);
+    cudaMemsetAsync(c->s.g[0], 0, Q * N * gsz, c->stream);
+    cudaMemsetAsync(c->s.f[1], 0, Q * N * 4, c->stream);
+    cudaMemsetAsync(c->s.g[1], 0, Q * N * gsz, c->stream);
+    cudaMemsetAsync(c->s.rho, 0, N * 4, c->stream);
+    cudaMemsetAsync(c->s.phi, 0, N * 4, c->stream);
+    c->type_host.assign(N, 0);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        dev_free_all(c->owned);
+        delete c;
+        return fail(TLB_E_CUDA, "create: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return TLB_OK;
+}
+
+extern "C" int tlb_create(int lattice, int nx, int ny, int nz, const double densities[2], const double kappas[3],
+                          const double viscosities[3], int wetting, const double angles_deg[3], tlb_ctx **out)
+{
+    if (!densities || !kappas || !viscosities || !angles_deg || !out) return fail(TLB_E_INVAL, "null argument");
+    tlb_params p;
+    tlb_params_default(&p);
+    p.lattice = lattice;
+    p.nx = nx;
+    p.ny = ny;
+    p.nz = nz;
+    p.rho_l = densities[0];
+    p.rho_g = densities[1];
+    for (int k = 0; k < 3; ++k) p.kappa[k] = kappas[k];
+    if (!(viscosities[0] == viscosities[1] && viscosities[1] == viscosities[2]))
+        return fail(TLB_E_UNSUPPORTED, "one kinematic viscosity for all phases (single beta)");
+    if (!(viscosities[0] > 0)) return fail(TLB_E_INVAL, "viscosity must be positive");
+    p.beta = 1.0 / (1.0 + 6.0 * viscosities[0]);   // nu = (1/beta - 1)/6
+    p.wetting = wetting;
+    for (int k = 0; k < 3; ++k) p.theta_deg[k] = angles_deg[k];
+    if (wetting == TLB_WET_FORCE)
+        for (int k = 0; k < 3; ++k)
+            if (angles_deg[k] != 90.0)
+                return fail(TLB_E_UNCALIBRATED, "force wetting: pass kappa^w through tlb_create_ex for angles != 90");
+    return tlb_create_ex(&p, out);
+}
+
+extern "C" void tlb_destroy(tlb_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    dev_free_all(c->owned);
+    delete c;
+}
+
+extern "C" int tlb_get_params(const tlb_ctx *c, tlb_params *out)
+{
+    if (!c || !out) return fail(TLB_E_INVAL, "null argument");
+    *out = c->p;
+    return TLB_OK;
+}
+
+extern "C" int tlb_get_derived(const tlb_ctx *c, tlb_derived *out)
+{
+    if (!c || !out) return fail(TLB_E_INVAL, "null argument");
+    *out = c->d;
+    return TLB_OK;
+}
+
+extern "C" int tlb_set_stream(tlb_ctx *c, void *stream)
+{
+    if (!c) return fail(TLB_E_INVAL, "null context");
+    c->stream = (cudaStream_t)stream;
+    return TLB_OK;
+}
+
+static inline long long nidx(const tlb_ctx *c, int x, int y, int z)
+{
+    int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    x = ((x % nx) + nx) % nx;
+    y = ((y % ny) + ny) % ny;
+    z = ((z % nz) + nz) % nz;
+    return (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+}
+
+extern "C" int tlb_set_solid(tlb_ctx *c, const uint8_t *mask)
+{
+    if (!c || !mask) return fail(TLB_E_INVAL, "null argument");
+    int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz, D = c->D;
+    long long N = c->N;
+    std::vector<uint8_t> t(N, 0);
+    for (long long n = 0; n < N; ++n) t[n] = mask[n] ? TLB_SOLID : 0;
+    c->ghost_host.clear();
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long long n = nidx(c, x, y, z);
+                bool solid = t[n] & TLB_SOLID;
+                bool touch = false;
+                int zr = D == 3 ? 1 : 0;
+                for (int dz = -zr; dz <= zr; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (!dx && !dy && !dz) continue;
+                            bool ns = mask[nidx(c, x + dx, y + dy, z + dz)] != 0;
+                            if (ns != solid) touch = true;
+                        }
+                uint8_t v = t[n];
+                if (solid && touch) {
+                    v |= TLB_GHOST;
+                    c->ghost_host.push_back((int)n);
+                }
+                if (!solid) {
+                    if (touch) v |= TLB_FIRST;
+                    if (mask[nidx(c, x + 1, y, z)] || mask[nidx(c, x - 1, y, z)]) v |= TLB_WALLX;
+                    if (mask[nidx(c, x, y + 1, z)] || mask[nidx(c, x, y - 1, z)]) v |= TLB_WALLY;
+                    if (D == 3 && (mask[nidx(c, x, y, z + 1)] || mask[nidx(c, x, y, z - 1)])) v |= TLB_WALLZ;
+                }
+                t[n] = v;
+            }
+    c->type_host = t;
+    CUDA_TRY(cudaMemcpyAsync(c->s.type, t.data(), N, cudaMemcpyHostToDevice, c->stream));
+    size_t ng = c->ghost_host.size();
+    if (ng > c->ghosts_cap) {
+        void *ptr;
+        int rc = dev_alloc(c->owned, &ptr, ng * sizeof(int), &c->bytes);
+        if (rc) return rc;
+        c->ghosts_dev = (int *)ptr;
+        c->ghosts_cap = ng;
+    }
+    if (ng) CUDA_TRY(cudaMemcpyAsync(c->ghosts_dev, c->ghost_host.data(), ng * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    c->s.ghosts = c->ghosts_dev;
+    c->s.nghost = (int)ng;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return TLB_OK;
+}
+
+static int check_status(tlb_ctx *c)
+{
+    unsigned st = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, c->s.status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (st) {
+        c->sticky = TLB_E_DIVERGED;
+        return fail(TLB_E_DIVERGED, "non-positive density or population met");
+    }
+    return TLB_OK;
+}
+
+extern "C" int tlb_sync(tlb_ctx *c)
+{
+    if (!c) return fail(TLB_E_INVAL, "null context");
+    return check_status(c);
+}
+
+static int init_from_device(tlb_ctx *c, const float *u_dev)
+{
+    DISPATCH(c, ghosts(c->dp, c->s, c->stream));
+    AuxOut none = {};
+    DISPATCH(c, step(c->dp, c->s, MODE_INIT, u_dev, none, c->stream));
+    c->steps = 0;
+    return check_launch(c, 2);
+}
+
+extern "C" int tlb_init_fields_device(tlb_ctx *c, const float *rho, const float *phi, const float *u)
+{
+    if (!c || !rho || !phi) return fail(TLB_E_INVAL, "null argument");
+    size_t N = (size_t)c->N;
+    CUDA_TRY(cudaMemcpyAsync(c->s.rho, rho, N * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->s.phi, phi, N * 4, cudaMemcpyDeviceToDevice, c->stream));
+    return init_from_device(c, u);
+}
+
+// temporary device buffer owned by one call
+struct Scratch {
+    void *p = nullptr;
+    ~Scratch()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+extern "C" int tlb_init_fields(tlb_ctx *c, const double *rho, const double *phi, const double *u)
+{
+    if (!c || !rho || !phi) return fail(TLB_E_INVAL, "null argument");
+    size_t N = (size_t)c->N;
+    std::vector<float> hr(N), hp(N), hu;
+    for (size_t n = 0; n < N; ++n) {
+        bool s = c->type_host[n] & TLB_SOLID;
+        hr[n] = s ? 0.f : (float)rho[n];
+        hp[n] = s ? 0.f : (float)phi[n];
+        if (!s && !(rho[n] > 0)) return fail(TLB_E_INVAL, "rho must be positive at fluid node %zu", n);
+    }
+    Scratch su;
+    if (u) {
+        hu.resize((size_t)c->D * N);
+        for (size_t k = 0; k < hu.size(); ++k) hu[k] = (float)u[k];
+        CUDA_TRY(cudaMalloc(&su.p, hu.size() * 4));
+        CUDA_TRY(cudaMemcpyAsync(su.p, hu.data(), hu.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->s.rho, hr.data(), N * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->s.phi, hp.data(), N * 4, cudaMemcpyHostToDevice, c->stream));
+    int rc = init_from_device(c, (const float *)su.p);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->sticky = TLB_OK;
+    return TLB_OK;
+}
+
+static void issue_step(tlb_ctx *c)
+{
+    AuxOut none = {};
+    DISPATCH(c, moments(c->dp, c->s, c->stream));
+    DISPATCH(c, ghosts(c->dp, c->s, c->stream));
+    DISPATCH(c, step(c->dp, c->s, MODE_STEP, nullptr, none, c->stream));
+    c->s.cur ^= 1;
+    c->steps += 1;
+    c->launches += (c->s.nghost > 0) ? 3 : 2;
+}
+
+extern "C" int tlb_step(tlb_ctx *c, int nsteps)
+{
+    if (!c) return fail(TLB_E_INVAL, "null context");
+    if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
+    for (int k = 0; k < nsteps; ++k) issue_step(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TLB_E_CUDA, "step launch: %s", cudaGetErrorString(e));
+    return c->sticky;
+}
+
+extern "C" int tlb_step_phase(tlb_ctx *c, int phase)
+{
+    if (!c) return fail(TLB_E_INVAL, "null context");
+    AuxOut none = {};
+    if (phase == 0) {
+        DISPATCH(c, moments(c->dp, c->s, c->stream));
+    } else if (phase == 1) {
+        DISPATCH(c, ghosts(c->dp, c->s, c->stream));
+        if (c->s.nghost == 0) return TLB_OK;
+    } else if (phase == 2) {
+        DISPATCH(c, step(c->dp, c->s, MODE_STEP, nullptr, none, c->stream));
+        c->s.cur ^= 1;
+        c->steps += 1;
+    } else {
+        return fail(TLB_E_INVAL, "phase must be 0, 1 or 2");
+    }
+    return check_launch(c, 1);
+}
+
+extern "C" int tlb_get_fields_device(tlb_ctx *c, float *rho, float *phi, float *u)
+{
+    if (!c) return fail(TLB_E_INVAL, "null context");
+    size_t N = (size_t)c->N;
+    DISPATCH(c, moments(c->dp, c->s, c->stream));
+    int nl = 1;
+    if (u) {
+        DISPATCH(c, fields(c->dp, c->s, u, c->stream));
+        ++nl;
+    }
+    if (rho) CUDA_TRY(cudaMemcpyAsync(rho, c->s.rho, N * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (phi) CUDA_TRY(cudaMemcpyAsync(phi, c->s.phi, N * 4, cudaMemcpyDeviceToDevice, c->stream));
+    return check_launch(c, nl);
+}
+
+extern "C" int tlb_get_fields(tlb_ctx *c, double *rho, double *phi, double *u, double *C)
+{
+    if (!c) return fail(TLB_E_INVAL, "null context");
+    size_t N = (size_t)c->N;
+    Scratch su;
+    std::vector<float> hr(N), hp(N), hu;
+    DISPATCH(c, moments(c->dp, c->s, c->stream));
+    int nl = 1;
+    if (u) {
+        CUDA_TRY(cudaMalloc(&su.p, (size_t)c->D * N * 4));
+        DISPATCH(c, fields(c->dp, c->s, (float *)su.p, c->stream));
+        ++nl;
+        hu.resize((size_t)c->D * N);
+        CUDA_TRY(cudaMemcpyAsync(hu.data(), su.p, hu.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CUDA_TRY(cudaMemcpyAsync(hr.data(), c->s.rho, N * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(hp.data(), c->s.phi, N * 4, cudaMemcpyDeviceToHost, c->stream));
+    int rc = check_launch(c, nl);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double rl = c->d.rho_l, rg = c->d.rho_g, chi = c->p.chi;
+    for (size_t n = 0; n < N; ++n) {
+        bool s = c->type_host[n] & TLB_SOLID;
+        double r = s ? 0.0 : hr[n], ph = s ? 0.0 : hp[n];
+        if (rho) rho[n] = r;
+        if (phi) phi[n] = ph;
+        if (u)
+            for (int a = 0; a < c->D; ++a) u[(size_t)a * N + n] = s ? 0.0 : hu[(size_t)a * N + n];
+        if (C) {
+            double C1 = (r - rl) / (rg - rl);
+            C[n] = s ? 0.0 : C1;
+            C[N + n] = s ? 0.0 : 0.5 * (1 + ph / chi - C1);
+            C[2 * N + n] = s ? 0.0 : 0.5 * (1 - ph / chi - C1);
+        }
+    }
+    return check_status(c);
+}
+
+extern "C" int tlb_diagnostics(tlb_ctx *c, double out[6])
+{
+    if (!c || !out) return fail(TLB_E_INVAL, "null argument");
+    DISPATCH(c, moments(c->dp, c->s, c->stream));
+    DISPATCH(c, diagnostics(c->dp, c->s, c->diag_part, c->diag_nb, c->diag_out, c->stream));
+    int rc = check_launch(c, 3);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(out, c->diag_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return TLB_OK;
+}
+
+extern "C" int tlb_get_aux(tlb_ctx *c, int which, double *out)
+{
+    if (!c || !out) return fail(TLB_E_INVAL, "null argument");
+    if (which < 0 || which > 13) return fail(TLB_E_INVAL, "which must be 0..13");
+    size_t N = (size_t)c->N;
+    Scratch sa;
+    DISPATCH(c, moments(c->dp, c->s, c->stream));
+    DISPATCH(c, ghosts(c->dp, c->s, c->stream));
+    int nl = 2;
+    const float *src = nullptr;
+    if (which == 12) src = c->s.rho;
+    else if (which == 13) src = c->s.phi;
+    else {
+        CUDA_TRY(cudaMalloc(&sa.p, N * 4));
+        CUDA_TRY(cudaMemsetAsync(sa.p, 0, N * 4, c->stream));
+        AuxOut a = {};
+        float *dst = (float *)sa.p;
+        if (which == 0) a.p0 = dst;
+        else if (which == 1) a.mur = dst;
+        else if (which == 2) a.mup = dst;
+        else if (which <= 5) a.F[which - 3] = dst;
+        else a.P[which - 6] = dst;
+        DISPATCH(c, step(c->dp, c->s, MODE_AUX, nullptr, a, c->stream));
+        ++nl;
+        src = dst;
+    }
+    std::vector<float> h(N);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), src, N * 4, cudaMemcpyDeviceToHost, c->stream));
+    int rc = check_launch(c, nl);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (size_t n = 0; n < N; ++n)
+        out[n] = ((c->type_host[n] & TLB_SOLID) && which < 12) ? 0.0 : (double)h[n];
+    return TLB_OK;
+}
+
+extern "C" int tlb_lattice_directions(int lattice, int *c, double *w)
+{
+    if (lattice != TLB_D2Q9 && lattice != TLB_D3Q27) return fail(TLB_E_INVAL, "bad lattice");
+    int Q = Qof(lattice), D = Dof(lattice);
+    for (int i = 0; i < Q; ++i) {
+        double wi = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            int v = (D == 2) ? (a < 2 ? cc<2>(i, a) : 0) : cc<3>(i, a);
+            if (c) c[3 * i + a] = v;
+            if (a < D) wi *= (v == 0) ? 2.0 / 3.0 : 1.0 / 6.0;
+        }
+        if (w) w[i] = wi;
+    }
+    return Q;
+}
+
+static int pop_io(tlb_ctx *c, double *f, double *g, const double *fi, const double *gi, int dir)
+{
+    size_t QN = (size_t)c->Q * (size_t)c->N;
+    Scratch s1, s2;
+    CUDA_TRY(cudaMalloc(&s1.p, QN * 8));
+    CUDA_TRY(cudaMalloc(&s2.p, QN * 8));
+    if (dir == 1) {
+        CUDA_TRY(cudaMemcpyAsync(s1.p, fi, QN * 8, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(s2.p, gi, QN * 8, cudaMemcpyHostToDevice, c->stream));
+    }
+    DISPATCH(c, convert_pop(c->dp, c->s, dir, (double *)s1.p, (double *)s2.p, c->stream));
+    int rc = check_launch(c, 1);
+    if (rc) return rc;
+    if (dir == 0) {
+        if (f) CUDA_TRY(cudaMemcpyAsync(f, s1.p, QN * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (g) CUDA_TRY(cudaMemcpyAsync(g, s2.p, QN * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return TLB_OK;
+}
+
+extern "C" int tlb_get_populations(tlb_ctx *c, double *f, double *g)
+{
+    if (!c) return fail(TLB_E_INVAL, "null context");
+    return pop_io(c, f, g, nullptr, nullptr, 0);
+}
+
+extern "C" int tlb_set_populations(tlb_ctx *c, const double *f, const double *g)
+{
+    if (!c || !f || !g) return fail(TLB_E_INVAL, "null argument");
+    return pop_io(c, nullptr, nullptr, f, g, 1);
+}
+
+struct SnapHeader {
+    uint64_t magic, N, Q, gbytes;
+    long long steps;
+};
+
+extern "C" size_t tlb_snapshot_bytes(const tlb_ctx *c)
+{
+    if (!c) return 0;
+    size_t QN = (size_t)c->Q * (size_t)c->N;
+    return sizeof(SnapHeader) + QN * 4 + QN * (c->p.g_fp16 ? 2 : 4);
+}
+
+extern "C" int tlb_snapshot(tlb_ctx *c, void *host, size_t bytes)
+{
+    if (!c || !host) return fail(TLB_E_INVAL, "null argument");
+    if (bytes < tlb_snapshot_bytes(c)) return fail(TLB_E_INVAL, "snapshot buffer too small");
+    size_t QN = (size_t)c->Q * (size_t)c->N, gb = QN * (c->p.g_fp16 ? 2 : 4);
+    SnapHeader h = {0x544c4253u, (uint64_t)c->N, (uint64_t)c->Q, (uint64_t)gb, c->steps};
+    std::memcpy(host, &h, sizeof(h));
+    char *dst = (char *)host + sizeof(h);
+    CUDA_TRY(cudaMemcpyAsync(dst, c->s.f[c->s.cur], QN * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(dst + QN * 4, c->s.g[c->s.cur], gb, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return TLB_OK;
+}
+
+extern "C" int tlb_restore(tlb_ctx *c, const void *host, size_t bytes)
+{
+    if (!c || !host) return fail(TLB_E_INVAL, "null argument");
+    if (bytes < tlb_snapshot_bytes(c)) return fail(TLB_E_INVAL, "snapshot buffer too small");
+    SnapHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    size_t QN = (size_t)c->Q * (size_t)c->N, gb = QN * (c->p.g_fp16 ? 2 : 4);
+    if (h.magic != 0x544c4253u || h.N != (uint64_t)c->N || h.Q != (uint64_t)c->Q || h.gbytes != gb)
+        return fail(TLB_E_INVAL, "snapshot does not match this context");
+    const char *src = (const char *)host + sizeof(h);
+    CUDA_TRY(cudaMemcpyAsync(c->s.f[c->s.cur], src, QN * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->s.g[c->s.cur], src + QN * 4, gb, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->steps = h.steps;
+    return TLB_OK;
+}
+
+extern "C" long long tlb_steps_done(const tlb_ctx *c) { return c ? c->steps : -1; }
+extern "C" size_t tlb_device_bytes(const tlb_ctx *c) { return c ? c->bytes : 0; }
+extern "C" long long tlb_launch_count(const tlb_ctx *c) { return c ? c->launches : -1; }
+
+// ---------------------------------------------------------------------------
+// batched stepping: one launch per phase over all lattices
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+    std::vector<tlb_ctx *> ctxs;
+    std::vector<Block> owned;
+    BatchEntry *entries[2] = {nullptr, nullptr};   // parity of the step
+    int4 *tiles = nullptr;
+    int2 *glist = nullptr;
+    int ntiles = 0, nglist = 0;
+};
+
+static int build_plan(tlb_ctx *const *ctxs, int n, BatchPlan &plan, cudaStream_t st)
+{
+    int D = ctxs[0]->D;
+    std::vector<int4> tiles;
+    std::vector<int2> gl;
+    std::vector<BatchEntry> e0(n), e1(n);
+    int TX = D == 2 ? Launch<2>::tile_dims(0) : Launch<3>::tile_dims(0);
+    int TY = D == 2 ? Launch<2>::tile_dims(1) : Launch<3>::tile_dims(1);
+    int TZ = D == 2 ? Launch<2>::tile_dims(2) : Launch<3>::tile_dims(2);
+    for (int k = 0; k < n; ++k) {
+        tlb_ctx *c = ctxs[k];
+        if (c->D != D) return fail(TLB_E_INVAL, "batched lattices must share the lattice type");
+        if (c->p.g_fp16) return fail(TLB_E_UNSUPPORTED, "batched stepping supports FP32 g only");
+        for (int par = 0; par < 2; ++par) {
+            BatchEntry &e = par ? e1[k] : e0[k];
+            int cur = (c->s.cur + par) & 1;
+            e.p = c->dp;
+            e.f_in = c->s.f[cur];
+            e.f_out = c->s.f[1 - cur];
+            e.g_in = c->s.g[cur];
+            e.g_out = c->s.g[1 - cur];
+            e.rho = c->s.rho;
+            e.phi = c->s.phi;
+            e.type = c->s.type;
+            e.status = c->s.status;
+        }
+        for (int z = 0; z < c->p.nz; z += TZ)
+            for (int y = 0; y < c->p.ny; y += TY)
+                for (int x = 0; x < c->p.nx; x += TX) tiles.push_back(make_int4(k, x, y, z));
+        for (int g : c->ghost_host) gl.push_back(make_int2(k, g));
+    }
+    void *ptr;
+    int rc;
+    if ((rc = dev_alloc(plan.owned, &ptr, n * sizeof(BatchEntry), nullptr))) return rc;
+    plan.entries[0] = (BatchEntry *)ptr;
+    if ((rc = dev_alloc(plan.owned, &ptr, n * sizeof(BatchEntry), nullptr))) return rc;
+    plan.entries[1] = (BatchEntry *)ptr;
+    if ((rc = dev_alloc(plan.owned, &ptr, tiles.size() * sizeof(int4), nullptr))) return rc;
+    plan.tiles = (int4 *)ptr;
+    if ((rc = dev_alloc(plan.owned, &ptr, std::max<size_t>(gl.size(), 1) * sizeof(int2), nullptr))) return rc;
+    plan.glist = (int2 *)ptr;
+    CUDA_TRY(cudaMemcpyAsync(plan.entries[0], e0.data(), n * sizeof(BatchEntry), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(plan.entries[1], e1.data(), n * sizeof(BatchEntry), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(plan.tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    if (!gl.empty()) CUDA_TRY(cudaMemcpyAsync(plan.glist, gl.data(), gl.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    plan.ntiles = (int)tiles.size();
+    plan.nglist = (int)gl.size();
+    plan.ctxs.assign(ctxs, ctxs + n);
+    return TLB_OK;
+}
+
+static int run_plan(BatchPlan &plan, int nsteps, cudaStream_t st)
+{
+    int D = plan.ctxs[0]->D;
+    for (int s = 0; s < nsteps; ++s) {
+        const BatchEntry *E = plan.entries[s & 1];
+        if (D == 2) {
+            Launch<2>::moments_batch(E, plan.tiles, plan.ntiles, st);
+            ghosts_batch_launch<2>(E, plan.glist, plan.nglist, st);
+            Launch<2>::step_batch(E, plan.tiles, plan.ntiles, st);
+        } else {
+            Launch<3>::moments_batch(E, plan.tiles, plan.ntiles, st);
+            ghosts_batch_launch<3>(E, plan.glist, plan.nglist, st);
+            Launch<3>::step_batch(E, plan.tiles, plan.ntiles, st);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TLB_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
+    int per = plan.nglist > 0 ? 3 : 2;
+    for (tlb_ctx *c : plan.ctxs) {
+        if (nsteps & 1) c->s.cur ^= 1;
+        c->steps += nsteps;
+    }
+    plan.ctxs[0]->launches += (long long)per * nsteps;
+    return TLB_OK;
+}
+
+extern "C" int tlb_step_batch(tlb_ctx *const *ctxs, int n, int nsteps)
+{
+    if (!ctxs || n <= 0 || nsteps < 0) return fail(TLB_E_INVAL, "bad batch arguments");
+    for (int k = 0; k < n; ++k)
+        if (!ctxs[k]) return fail(TLB_E_INVAL, "null context in batch");
+    cudaStream_t st = ctxs[0]->stream;
+    BatchPlan plan;
+    int rc = build_plan(ctxs, n, plan, st);
+    if (rc == TLB_OK) rc = run_plan(plan, nsteps, st);
+    cudaStreamSynchronize(st);
+    dev_free_all(plan.owned);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// request server: continuous batching with admission by device-memory budget
+// ---------------------------------------------------------------------------
+namespace {
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+    uint64_t ticket;
+    tlb_params params;
+    std::vector<uint8_t> mask;
+    std::vector<double> rho, phi;
+    int nsteps, done_steps = 0;
+    tlb_ctx *ctx = nullptr;
+    tlb_result res;
+    size_t bytes = 0;
+    std::vector<double> out_rho, out_phi;
+};
+}  // namespace
+
+struct tlb_server {
+    size_t budget;
+    int max_active, steps_per_round;
+    cudaStream_t stream;
+    uint64_t next = 1;
+    std::deque<Req *> queue;
+    std::vector<Req *> active;
+    std::map<uint64_t, Req *> all;
+    size_t in_use = 0;
+    std::mutex mu;
+};
+
+static size_t footprint(const tlb_params &p)
+{
+    size_t N = (size_t)p.nx * p.ny * p.nz, Q = (size_t)Qof(p.lattice);
+    return 2 * Q * N * 4 + 2 * Q * N * (p.g_fp16 ? 2 : 4) + N * 9 + (1 << 16);
+}
+
+extern "C" int tlb_server_create(size_t budget, int max_active, int steps_per_round, void *stream, tlb_server **out)
+{
+    if (!out || budget == 0 || max_active <= 0 || steps_per_round <= 0) return fail(TLB_E_INVAL, "bad server arguments");
+    tlb_server *s = new tlb_server();
+    s->budget = budget;
+    s->max_active = max_active;
+    s->steps_per_round = steps_per_round;
+    s->stream = (cudaStream_t)stream;
+    *out = s;
+    return TLB_OK;
+}
+
+extern "C" int tlb_submit(tlb_server *s, const tlb_request *r, uint64_t *ticket)
+{
+    if (!s || !r || !ticket || !r->rho || !r->phi || r->nsteps < 0) return fail(TLB_E_INVAL, "bad request");
+    int rc = validate(r->params);
+    if (rc) return rc;
+    size_t fp = footprint(r->params);
+    if (fp > s->budget) return fail(TLB_E_INVAL, "request needs %zu bytes, budget is %zu", fp, s->budget);
+    size_t N = (size_t)r->params.nx * r->params.ny * r->params.nz;
+    Req *q = new Req();
+    q->params = r->params;
+    if (r->mask) q->mask.assign(r->mask, r->mask + N);
+    q->rho.assign(r->rho, r->rho + N);
+    q->phi.assign(r->phi, r->phi + N);
+    q->nsteps = r->nsteps;
+    q->bytes = fp;
+    std::memset(&q->res, 0, sizeof(q->res));
+    q->res.state = TLB_REQ_QUEUED;
+    q->res.submit_s = now_s();
+    std::lock_guard<std::mutex> lk(s->mu);
+    q->ticket = s->next++;
+    s->queue.push_back(q);
+    s->all[q->ticket] = q;
+    *ticket = q->ticket;
+    return TLB_OK;
+}
+
+static void retire(tlb_server *s, Req *q, int status)
+{
+    if (q->ctx) {
+        if (status == TLB_OK) {
+            size_t N = (size_t)q->ctx->N;
+            q->out_rho.resize(N);
+            q->out_phi.resize(N);
+            int rc = tlb_get_fields(q->ctx, q->out_rho.data(), q->out_phi.data(), nullptr, nullptr);
+            if (rc == TLB_OK) rc = tlb_diagnostics(q->ctx, q->res.mass);
+            status = rc;
+        }
+        tlb_destroy(q->ctx);
+        q->ctx = nullptr;
+    }
+    s->in_use -= q->bytes;
+    q->res.status = status;
+    q->res.state = status == TLB_OK ? TLB_REQ_DONE : TLB_REQ_FAILED;
+    q->res.done_s = now_s();
+}
+
+extern "C" int tlb_server_pump(tlb_server *s)
+{
+    if (!s) return fail(TLB_E_INVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    // admit in arrival order while memory and slots allow (no overtaking)
+    while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
+        Req *q = s->queue.front();
+        if (s->in_use + q->bytes > s->budget) break;
+        s->queue.pop_front();
+        s->in_use += q->bytes;
+        q->res.state = TLB_REQ_RUNNING;
+        q->res.start_s = now_s();
+        int rc = tlb_create_ex(&q->params, &q->ctx);
+        if (rc == TLB_OK) rc = tlb_set_stream(q->ctx, s->stream);
+        if (rc == TLB_OK && !q->mask.empty()) rc = tlb_set_solid(q->ctx, q->mask.data());
+        if (rc == TLB_OK) rc = tlb_init_fields(q->ctx, q->rho.data(), q->phi.data(), nullptr);
+        q->mask.clear();
+        q->rho.clear();
+        q->phi.clear();
+        if (rc != TLB_OK) { retire(s, q, rc); continue; }
+        if (q->nsteps == 0) { retire(s, q, TLB_OK); continue; }
+        s->active.push_back(q);
+    }
+    if (s->active.empty()) return 0;
+    // advance the active lattices together, grouped by lattice type and g storage
+    int chunk = s->steps_per_round;
+    for (Req *q : s->active) chunk = std::min(chunk, q->nsteps - q->done_steps);
+    std::vector<tlb_ctx *> groups[2];
+    for (Req *q : s->active) {
+        if (q->ctx->p.g_fp16) {
+            tlb_step(q->ctx, chunk);
+            continue;
+        }
+        groups[q->ctx->D == 3].push_back(q->ctx);
+    }
+    for (int g = 0; g < 2; ++g)
+        if (!groups[g].empty()) {
+            int rc = tlb_step_batch(groups[g].data(), (int)groups[g].size(), chunk);
+            if (rc) return rc;
+        }
+    std::vector<Req *> still;
+    for (Req *q : s->active) {
+        q->done_steps += chunk;
+        if (q->done_steps >= q->nsteps) {
+            int rc = tlb_sync(q->ctx);
+            retire(s, q, rc);
+        } else {
+            still.push_back(q);
+        }
+    }
+    s->active.swap(still);
+    return (int)s->active.size();
+}
+
+extern "C" int tlb_poll(tlb_server *s, uint64_t ticket, tlb_result *res, double *rho, double *phi)
+{
+    if (!s || !res) return fail(TLB_E_INVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return fail(TLB_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Req *q = it->second;
+    *res = q->res;
+    if (q->res.state == TLB_REQ_DONE || q->res.state == TLB_REQ_FAILED) {
+        if (rho && !q->out_rho.empty()) std::memcpy(rho, q->out_rho.data(), q->out_rho.size() * 8);
+        if (phi && !q->out_phi.empty()) std::memcpy(phi, q->out_phi.data(), q->out_phi.size() * 8);
+        s->all.erase(it);
+        delete q;
+    }
+    return TLB_OK;
+}
+
+extern "C" int tlb_server_stats(tlb_server *s, int *queued, int *active, size_t *bytes)
+{
+    if (!s) return fail(TLB_E_INVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (queued) *queued = (int)s->queue.size();
+    if (active) *active = (int)s->active.size();
+    if (bytes) *bytes = s->in_use;
+    return TLB_OK;
+}
+
+extern "C" void tlb_server_destroy(tlb_server *s)
+{
+    if (!s) return;
+    for (Req *q : s->active)
+        if (q->ctx) tlb_destroy(q->ctx);
+    for (auto &kv : s->all) delete kv.second;
+    delete s;
+}

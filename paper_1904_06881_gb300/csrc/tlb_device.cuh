@@ -1,0 +1,309 @@
+// tlb_device.cuh -- device code of the ternary free-energy ELBM step
+// (arXiv:1904.06881, Sec. II-IV) for sm_103a.  Included by one translation
+// unit per lattice (tlb_d2q9.cu, tlb_d3q27.cu).
+//
+// Data layout in HBM (one lattice of N nodes, x fastest, periodic):
+//   f  : float[Q][N]  pre-collision populations stored as f_i - w_i
+//   g  : float[Q][N]  (or half[Q][N] scaled by 1/chi) order-parameter populations
+//   rho, phi : float[N] moments of the current state; solid ghost nodes hold
+//              the ghost-layer values of Sec. IV
+//   type : uint8[N]  node flags (TLB_SOLID, TLB_FIRST, TLB_GHOST, wall axes)
+// One step = three launches:
+//   moments_kernel  : rho = 1 + sum_i f~_i, phi = sum_i g_i       (reads 2Q floats)
+//   ghost_kernel    : ghost-layer rho, phi over the ghost-node list  (small)
+//   step_kernel     : tile + halo of rho, phi in shared memory -> stencils,
+//                     chemical potentials, pressure tensor (halo 1) -> force
+//                     with wall rules -> ELBM collision of f (entropic alpha),
+//                     LBGK of g -> push streaming with halfway bounce-back.
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "tlb_internal.h"
+
+namespace tlb {
+
+// ---------------------------------------------------------------------------
+// Lattice tables (own enumeration: rest, then +c/-c pairs).
+// ---------------------------------------------------------------------------
+template <int D>
+struct Lat;
+
+template <>
+struct Lat<2> {
+    static constexpr int Q = 9;
+    static constexpr int NPOS = 4;
+    __host__ __device__ static constexpr int pos(int k, int a)
+    {
+        // positive directions: (1,0) (0,1) (1,1) (1,-1)
+        return a == 2 ? 0 : (k == 0 ? (a == 0 ? 1 : 0) : k == 1 ? (a == 0 ? 0 : 1) : k == 2 ? 1 : (a == 0 ? 1 : -1));
+    }
+};
+
+template <>
+struct Lat<3> {
+    static constexpr int Q = 27;
+    static constexpr int NPOS = 13;
+    __host__ __device__ static constexpr int pos(int k, int a)
+    {
+        // (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)
+        // (1,1,1) (1,1,-1) (1,-1,1) (1,-1,-1)
+        constexpr int t[13][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1},
+                                  {0, 1, 1}, {0, 1, -1}, {1, 1, 1}, {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+        return t[k][a];
+    }
+};
+
+template <int D>
+__host__ __device__ constexpr int cc(int i, int a)
+{
+    return i == 0 ? 0 : ((i - 1) % 2 == 0 ? Lat<D>::pos((i - 1) / 2, a) : -Lat<D>::pos((i - 1) / 2, a));
+}
+
+template <int D>
+__host__ __device__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : ((i - 1) % 2 == 0 ? i + 1 : i - 1);
+}
+
+// weights: product of D1Q3 weights 2/3 (c = 0) and 1/6 (c = +-1)
+template <int D>
+__host__ __device__ constexpr float wt(int i)
+{
+    float w = 1.0f;
+    for (int a = 0; a < D; ++a) w *= (cc<D>(i, a) == 0) ? (2.0f / 3.0f) : (1.0f / 6.0f);
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrapi(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ long long node_of(const DevParams &p, int x, int y, int z)
+{
+    return (long long)wrapi(x, p.nx) + (long long)p.nx * ((long long)wrapi(y, p.ny) + (long long)p.ny * wrapi(z, p.nz));
+}
+
+// ---------------------------------------------------------------------------
+// Thermodynamics (Sec. II.A-B), FP32
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float gpoly(float x) { return x * (x - 0.5f) * (x - 1.0f); }
+
+struct Bulk {
+    float murB, mupB, p0;
+};
+
+// Bulk chemical potentials and pressure at (rho, phi): Eqs. BulkEnergy,
+// bulkchempotrho (lambda_2 term with the sign of the derivative of
+// Eq. BulkEnergy), bulkchempotphi, bulkpressure, with the Carnahan-Starling
+// Psi of Eq. PsiEOS and its printed derivative.
+__device__ __forceinline__ Bulk bulk_terms(const DevParams &p, float rho, float phi)
+{
+    float C1 = (rho - p.rho_l) * p.inv_rgl;            // (rho - rho_l)/(rho_g - rho_l)
+    float C2 = 0.5f * (1.0f + phi * p.inv_chi - C1);
+    float C3 = 0.5f * (1.0f - phi * p.inv_chi - C1);
+    float br = p.b * rho;
+    float q = br - 4.0f;
+    float lr = __logf(rho);
+    float psi = rho * (p.C - p.a * rho - 8.0f * p.RT * (br - 6.0f) / (q * q) + p.RT * lr);
+    float dpsi = p.C - 2.0f * p.a * rho + p.RT * (1.0f + lr) + 16.0f * p.RT * (br - 12.0f) / (q * q * q);
+    float g2 = gpoly(C2), g3 = gpoly(C3);
+    float fb = 0.5f * p.lam1 * (psi - p.Psi0) + 0.5f * p.lam2 * C2 * C2 * (1.0f - C2) * (1.0f - C2) +
+               0.5f * p.lam3 * C3 * C3 * (1.0f - C3) * (1.0f - C3);
+    Bulk r;
+    r.murB = 0.5f * p.lam1 * dpsi + (p.lam2 * g2 + p.lam3 * g3) * p.inv_drho;
+    r.mupB = (p.lam2 * g2 - p.lam3 * g3) * p.inv_chi;
+    r.p0 = rho * r.murB + phi * r.mupB - fb;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Product-form equilibrium (Eqs. eqrho, A, B): per axis the three D1Q3
+// factors w(c) A(u) B(u)^c, c = 0, +1, -1.
+// ---------------------------------------------------------------------------
+struct Fac {
+    float f0, fp, fm;
+};
+
+__device__ __forceinline__ Fac eq_factors(float u)
+{
+    float s = sqrtf(1.0f + 3.0f * u * u);
+    float A = 2.0f - s;
+    float B = (2.0f * u + s) / (1.0f - u);
+    Fac r;
+    r.f0 = (2.0f / 3.0f) * A;
+    r.fp = (1.0f / 6.0f) * A * B;
+    r.fm = (1.0f / 6.0f) * A / B;
+    return r;
+}
+
+__device__ __forceinline__ float fac_of(const Fac &f, int c) { return c == 0 ? f.f0 : (c > 0 ? f.fp : f.fm); }
+
+// phi(y) = (1 + y) ln(1 + y) - y, accurate for small |y| (series y^2/2 - y^3/6 + ...)
+__device__ __forceinline__ float phi_ent(float y)
+{
+    if (fabsf(y) < 1e-2f) return y * y * (0.5f + y * (-1.0f / 6.0f + y * (1.0f / 12.0f - y * (1.0f / 20.0f))));
+    return (1.0f + y) * log1pf(y) - y;
+}
+
+// Entropic alpha: non-trivial root of H(f' + alpha D) = H(f') (Eq. EntropyEquation)
+// with D = f^eq(u) - f = f^eq(u + du) - f'.  Because ln(f^eq_i(u+du)/w_i) is
+// affine in c_i and D has no mass or momentum,
+//   h(alpha) = alpha S1 + sum_i f'_i phi(alpha x_i),  x_i = D_i/f'_i,
+//   S1 = sum_i D_i ln(1 - D_i/f^eq_i(u+du)),
+// a form with no cancellation between O(1) entropies.  Newton from alpha = 2,
+// bracketed by [1, alpha_max) where alpha_max keeps every population
+// positive.  Near the interface (max |x| > 1e-2) the sums and the Newton ratio
+// are accumulated in FP64.
+template <int Q, typename Acc>
+__device__ __forceinline__ float alpha_solve(const float (&fp)[Q], const float (&dl)[Q], float amax)
+{
+    Acc S1 = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float feqd = fp[i] + dl[i];
+        S1 += (Acc)(dl[i] * log1pf(-dl[i] / feqd));
+    }
+    float lo = 1.0f, hi = amax * (1.0f - 1e-6f);
+    auto hval = [&](float al, Acc &dh) {
+        Acc h = (Acc)al * S1;
+        dh = S1;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float y = al * (dl[i] / fp[i]);
+            h += (Acc)(fp[i] * phi_ent(y));
+            dh += (Acc)(dl[i] * log1pf(y));
+        }
+        return h;
+    };
+    Acc dh;
+    if (hi < 4.0f) {
+        if (hval(hi, dh) < (Acc)0) return hi;       // no root below the positivity bound
+    }
+    float al = 2.0f;
+    if (!(al > lo && al < hi)) al = 0.5f * (lo + hi);
+    for (int it = 0; it < 24; ++it) {
+        Acc h = hval(al, dh);
+        if (h > (Acc)0) hi = al; else lo = al;
+        float nxt = (dh != (Acc)0) ? (float)((Acc)al - h / dh) : 0.5f * (lo + hi);
+        if (!(nxt > lo && nxt < hi)) nxt = 0.5f * (lo + hi);
+        if (fabsf(nxt - al) <= 2e-7f * al) { al = nxt; break; }
+        al = nxt;
+        if (hi - lo <= 4e-7f * hi) break;
+    }
+    return al;
+}
+
+// ---------------------------------------------------------------------------
+// Ghost layer (Sec. IV): one fluid-facing direction of a ghost node.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ bool is_fluid(const uint8_t *type, long long n)
+{
+    return !(type[n] & TLB_SOLID);
+}
+
+template <int D>
+__device__ void ghost_axis(const DevParams &p, const uint8_t *__restrict__ type, const float *__restrict__ rho,
+                           const float *__restrict__ phi, int yx, int yy, int yz, int axis, float &gr, float &gp)
+{
+    long long y = node_of(p, yx, yy, yz);
+    float r1 = rho[y], p1 = phi[y];
+    if (p.wetting == TLB_WET_FORCE) { gr = r1; gp = p1; return; }
+    int T[2];
+    int nt = 0;
+    for (int t = 0; t < D; ++t)
+        if (t != axis) T[nt++] = t;
+    float dr[2] = {0.f, 0.f}, dp[2] = {0.f, 0.f};
+    int yc[3] = {yx, yy, yz};
+    for (int k = 0; k < nt; ++k) {
+        int cp[3] = {yc[0], yc[1], yc[2]}, cm[3] = {yc[0], yc[1], yc[2]};
+        cp[T[k]] += 1;
+        cm[T[k]] -= 1;
+        long long np_ = node_of(p, cp[0], cp[1], cp[2]), nm = node_of(p, cm[0], cm[1], cm[2]);
+        bool fp_ = is_fluid<D>(type, np_), fm = is_fluid<D>(type, nm);
+        if (fp_ && fm) { dr[k] = 0.5f * (rho[np_] - rho[nm]); dp[k] = 0.5f * (phi[np_] - phi[nm]); }
+        else if (fp_) { dr[k] = rho[np_] - r1; dp[k] = phi[np_] - p1; }
+        else if (fm) { dr[k] = r1 - rho[nm]; dp[k] = p1 - phi[nm]; }
+    }
+    float nr = 0.f, npp = 0.f, dot = 0.f;
+    for (int k = 0; k < nt; ++k) { nr += dr[k] * dr[k]; npp += dp[k] * dp[k]; dot += dr[k] * dp[k]; }
+    nr = sqrtf(nr);
+    npp = sqrtf(npp);
+    // interface identification (Sec. IV.B): 0 = 1-2, 1 = 1-3, 2 = 2-3
+    int pair;
+    if (nr < 0.01f * (p.rho_l - p.rho_g) * p.inv_chi * npp) pair = 2;
+    else if (r1 > 0.5f * p.rho_l && p1 < -0.95f * p.chi) pair = 1;
+    else if (r1 > 0.5f * p.rho_l && p1 > 0.95f * p.chi) pair = 0;
+    else if (dot < 0.f) pair = 1;
+    else pair = 0;
+    const float *dc = (pair == 2) ? dp : dr;
+    float nc = (pair == 2) ? npp : nr;
+    float cot = p.cot[pair];
+    if (!(nc > 1e-12f)) { gr = r1; gp = p1; return; }
+    float tx = dc[0] / nc, ty = (nt > 1) ? dc[1] / nc : 0.f;
+    if (p.wetting == TLB_WET_GEOM_EXTRAP) {
+        // Eqs. geomamgle, geomding; the second field follows the same interface
+        float sr = dr[0] * tx + (nt > 1 ? dr[1] * ty : 0.f);
+        float sp = dp[0] * tx + (nt > 1 ? dp[1] * ty : 0.f);
+        gr = r1 + cot * sr;
+        gp = p1 + cot * sp;
+        return;
+    }
+    // geometric interpolation: sample at cot(theta) t_hat in the first fluid layer
+    auto samp = [&](int k1, int k2, float &vr, float &vp) {
+        int q[3] = {yc[0], yc[1], yc[2]};
+        q[T[0]] += k1;
+        if (nt > 1) q[T[1]] += k2;
+        long long m = node_of(p, q[0], q[1], q[2]);
+        if (is_fluid<D>(type, m)) { vr = rho[m]; vp = phi[m]; }
+        else { vr = r1; vp = p1; }
+    };
+    if (nt == 1) {
+        float l = cot * tx;
+        int l0 = (int)floorf(l), l1 = l0 + 1;
+        float v0r, v0p, v1r, v1p;
+        samp(l0, 0, v0r, v0p);
+        samp(l1, 0, v1r, v1p);
+        float t = l - (float)l0;                 // linear interpolation on [l0, l1] (Eq. interp2D)
+        gr = v0r + t * (v1r - v0r);
+        gp = v0p + t * (v1p - v0p);
+        return;
+    }
+    float lx = cot * tx, ly = cot * ty;
+    if (sqrtf(lx * lx + ly * ly) < 1e-12f) { gr = r1; gp = p1; return; }
+    int X0 = (int)floorf(lx), Y0 = (int)floorf(ly);
+    // of the four corners of the unit cell around (lx, ly), drop the one nearest
+    // to the origin (first of (0,0),(1,0),(0,1),(1,1) on ties) (Eq. interp3D)
+    int drop = 0;
+    int best = 1 << 30;
+    for (int k = 0; k < 4; ++k) {
+        int cx = X0 + (k & 1), cy = Y0 + (k >> 1);
+        int d2 = cx * cx + cy * cy;
+        if (d2 < best) { best = d2; drop = k; }
+    }
+    float xs[3], ys[3], vr[3], vp[3];
+    int m = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (k == drop) continue;
+        int cx = X0 + (k & 1), cy = Y0 + (k >> 1);
+        xs[m] = (float)cx;
+        ys[m] = (float)cy;
+        samp(cx, cy, vr[m], vp[m]);
+        ++m;
+    }
+    // barycentric coordinates of (lx, ly) in the triangle
+    float e1x = xs[1] - xs[0], e1y = ys[1] - ys[0], e2x = xs[2] - xs[0], e2y = ys[2] - ys[0];
+    float det = e1x * e2y - e2x * e1y;
+    float px = lx - xs[0], py = ly - ys[0];
+    float b1 = (px * e2y - e2x * py) / det, b2 = (e1x * py - px * e1y) / det;
+    gr = vr[0] + b1 * (vr[1] - vr[0]) + b2 * (vr[2] - vr[0]);
+    gp = vp[0] + b1 * (vp[1] - vp[0]) + b2 * (vp[2] - vp[0]);
+}
+
+}  // namespace tlb

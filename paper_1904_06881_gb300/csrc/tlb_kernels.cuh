@@ -1,0 +1,707 @@
+// tlb_kernels.cuh -- kernels and launchers of the ternary ELBM step, templated
+// on the dimension D (D2Q9 / D3Q27).  Instantiated once per lattice.
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "tlb_device.cuh"
+
+namespace tlb {
+
+// ---- g storage: FP32, or FP16 scaled by 1/chi ----
+template <typename GT>
+struct GIO;
+template <>
+struct GIO<float> {
+    static __device__ __forceinline__ float ld(const void *p, long long k, float) { return __ldg((const float *)p + k); }
+    static __device__ __forceinline__ void st(void *p, long long k, float v, float) { ((float *)p)[k] = v; }
+};
+template <>
+struct GIO<__half> {
+    static __device__ __forceinline__ float ld(const void *p, long long k, float unscale)
+    {
+        return __half2float(((const __half *)p)[k]) * unscale;
+    }
+    static __device__ __forceinline__ void st(void *p, long long k, float v, float scale)
+    {
+        ((__half *)p)[k] = __float2half_rn(v * scale);
+    }
+};
+
+template <int D>
+struct Tile;
+template <>
+struct Tile<2> {
+    static constexpr int X = 32, Y = 8, Z = 1;
+};
+template <>
+struct Tile<3> {
+    static constexpr int X = 16, Y = 8, Z = 2;
+};
+
+// ---------------------------------------------------------------------------
+// moments: rho = 1 + sum_i (f_i - w_i), phi = sum_i g_i at fluid nodes
+// ---------------------------------------------------------------------------
+template <int D, typename GT>
+__device__ __forceinline__ void moments_node(const DevParams &p, const float *__restrict__ f, const void *g,
+                                             const uint8_t *__restrict__ type, float *rho, float *phi, long long n)
+{
+    constexpr int Q = Lat<D>::Q;
+    if (type[n] & TLB_SOLID) {
+        if (!(type[n] & TLB_GHOST)) { rho[n] = 0.f; phi[n] = 0.f; }
+        return;
+    }
+    float r = 0.f, ph = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        r += __ldg(f + (long long)i * p.N + n);
+        ph += GIO<GT>::ld(g, (long long)i * p.N + n, p.g_unscale);
+    }
+    rho[n] = 1.0f + r;
+    phi[n] = ph;
+}
+
+template <int D, typename GT>
+__global__ void __launch_bounds__(256) moments_kernel(DevParams p, const float *__restrict__ f, const void *g,
+                                                      const uint8_t *__restrict__ type, float *rho, float *phi)
+{
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < p.N; n += (long long)gridDim.x * blockDim.x)
+        moments_node<D, GT>(p, f, g, type, rho, phi, n);
+}
+
+template <int D, typename GT>
+__global__ void __launch_bounds__(256) moments_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
+{
+    int4 t = tiles[blockIdx.x];
+    const BatchEntry &e = E[t.x];
+    constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+    int lx = threadIdx.x % TX, ly = (threadIdx.x / TX) % TY, lz = threadIdx.x / (TX * TY);
+    int x = t.y + lx, y = t.z + ly, z = t.w + lz;
+    if (x >= e.p.nx || y >= e.p.ny || z >= e.p.nz) return;
+    long long n = (long long)x + (long long)e.p.nx * ((long long)y + (long long)e.p.ny * z);
+    moments_node<D, GT>(e.p, e.f_in, e.g_in, e.type, const_cast<float *>(e.rho), const_cast<float *>(e.phi), n);
+}
+
+// ---------------------------------------------------------------------------
+// ghost layer (Sec. IV): average over fluid-facing axis directions; ghosts
+// with only diagonal fluid neighbours take the mean of those neighbours.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ void ghost_node(const DevParams &p, const uint8_t *__restrict__ type, float *rho, float *phi, long long n)
+{
+    constexpr int Q = Lat<D>::Q;
+    int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+    int c[3] = {x, y, z};
+    float sr = 0.f, sp = 0.f;
+    int cnt = 0;
+    for (int a = 0; a < D; ++a)
+        for (int s = -1; s <= 1; s += 2) {
+            int q[3] = {c[0], c[1], c[2]};
+            q[a] += s;
+            long long m = node_of(p, q[0], q[1], q[2]);
+            if (type[m] & TLB_SOLID) continue;
+            float gr, gp;
+            ghost_axis<D>(p, type, rho, phi, wrapi(q[0], p.nx), wrapi(q[1], p.ny), wrapi(q[2], p.nz), a, gr, gp);
+            sr += gr;
+            sp += gp;
+            ++cnt;
+        }
+    if (cnt == 0) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            long long m = node_of(p, x + cc<D>(i, 0), y + cc<D>(i, 1), z + cc<D>(i, 2));
+            if (type[m] & TLB_SOLID) continue;
+            sr += rho[m];
+            sp += phi[m];
+            ++cnt;
+        }
+    }
+    if (cnt > 0) {
+        rho[n] = sr / (float)cnt;
+        phi[n] = sp / (float)cnt;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) ghost_kernel(DevParams p, const uint8_t *__restrict__ type, float *rho, float *phi,
+                                                    const int *__restrict__ ghosts, int nghost)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nghost) return;
+    ghost_node<D>(p, type, rho, phi, ghosts[k]);
+}
+
+// batched ghost list: (entry, node)
+template <int D>
+__global__ void __launch_bounds__(128) ghost_batch_kernel(const BatchEntry *__restrict__ E, const int2 *__restrict__ gl, int n)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int2 q = gl[k];
+    const BatchEntry &e = E[q.x];
+    ghost_node<D>(e.p, e.type, const_cast<float *>(e.rho), const_cast<float *>(e.phi), q.y);
+}
+
+// ---------------------------------------------------------------------------
+// Node thermodynamics from a shared-memory tile of rho, phi (halo 2).
+// ---------------------------------------------------------------------------
+template <int D>
+struct Thermo {
+    float gr[3], gp[3], lr, lp;
+    Bulk b;
+    float mur, mup;
+    float P[6];     // xx yy zz xy xz yz
+};
+
+template <int D, int RX, int RY>
+__device__ __forceinline__ Thermo<D> node_thermo(const DevParams &p, const float *srho, const float *sphi, int hx,
+                                                 int hy, int hz)
+{
+    constexpr int Q = Lat<D>::Q;
+    Thermo<D> t;
+    int c0 = hx + RX * (hy + RY * hz);
+    float r0 = srho[c0], p0v = sphi[c0];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { t.gr[a] = 0.f; t.gp[a] = 0.f; }
+    t.lr = 0.f;
+    t.lp = 0.f;
+    // grad Q = 3 sum w_i c_i Q(x + c_i); lap Q = 6 sum w_i (Q(x + c_i) - Q(x))
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        int m = (hx + cc<D>(i, 0)) + RX * ((hy + cc<D>(i, 1)) + RY * (hz + cc<D>(i, 2)));
+        float rm = srho[m], pm = sphi[m];
+        float w3 = 3.0f * wt<D>(i);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            if (cc<D>(i, a) != 0) {
+                t.gr[a] += (float)cc<D>(i, a) * w3 * rm;
+                t.gp[a] += (float)cc<D>(i, a) * w3 * pm;
+            }
+        }
+        t.lr += 2.0f * w3 * (rm - r0);
+        t.lp += 2.0f * w3 * (pm - p0v);
+    }
+    t.b = bulk_terms(p, r0, p0v);
+    t.mur = t.b.murB - p.krr * t.lr - p.krp * t.lp;
+    t.mup = t.b.mupB - p.kpp * t.lp - p.krp * t.lr;
+    float g2r = 0.f, g2p = 0.f, grp = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        g2r += t.gr[a] * t.gr[a];
+        g2p += t.gp[a] * t.gp[a];
+        grp += t.gr[a] * t.gp[a];
+    }
+    float iso = t.b.p0 - p.krr * (r0 * t.lr + 0.5f * g2r) - p.kpp * (p0v * t.lp + 0.5f * g2p) -
+                p.krp * (r0 * t.lp + p0v * t.lr + grp);
+    constexpr int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        int a = pa[k], b = pb[k];
+        float v = 0.f;
+        if (a < D && b < D) {
+            v = p.krr * t.gr[a] * t.gr[b] + p.kpp * t.gp[a] * t.gp[b] + p.krp * (t.gr[a] * t.gp[b] + t.gp[a] * t.gr[b]);
+            if (a == b) v += iso;
+        }
+        t.P[k] = v;
+    }
+    return t;
+}
+
+template <int D>
+__host__ __device__ constexpr int NQC() { return D == 2 ? 3 : 6; }
+
+// index into the Q-tensor components stored per node: 2D {xx, yy, xy}, 3D {xx, yy, zz, xy, xz, yz}
+template <int D>
+__device__ __forceinline__ int qcomp(int a, int b)
+{
+    if (a == b) return a;
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    if (D == 2) return 2;
+    return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+
+// ---------------------------------------------------------------------------
+// The fused step kernel.  One CTA = one tile of TX x TY x TZ nodes.
+// ---------------------------------------------------------------------------
+template <int D, typename GT, int MODE>
+__device__ __forceinline__ void step_tile(const DevParams &p, const float *__restrict__ f_in, float *__restrict__ f_out,
+                                          const void *g_in, void *g_out, const float *__restrict__ rho,
+                                          const float *__restrict__ phi, const uint8_t *__restrict__ type,
+                                          unsigned *status, int x0, int y0, int z0, const float *__restrict__ u_init,
+                                          const AuxOut &aux)
+{
+    constexpr int Q = Lat<D>::Q;
+    constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+    constexpr int RX = TX + 4, RY = TY + 4, RZ = (D == 3) ? TZ + 4 : 1;
+    constexpr int SX = TX + 2, SY = TY + 2, SZ = (D == 3) ? TZ + 2 : 1;
+    constexpr int NR = RX * RY * RZ, NS = SX * SY * SZ;
+    constexpr int HZ2 = (D == 3) ? 2 : 0, HZ1 = (D == 3) ? 1 : 0;
+    constexpr int NC = NQC<D>();
+    __shared__ float srho[NR], sphi[NR];
+    __shared__ float sQ[NC][NS];
+    __shared__ float smu[NS];
+    __shared__ uint8_t stype[NS];
+    const int tid = threadIdx.x;
+
+    // Stage A: rho, phi of the tile + halo 2; node flags of the tile + halo 1
+    for (int k = tid; k < NR; k += blockDim.x) {
+        int lx = k % RX, ly = (k / RX) % RY, lz = k / (RX * RY);
+        long long n = node_of(p, x0 - 2 + lx, y0 - 2 + ly, z0 - HZ2 + lz);
+        srho[k] = __ldg(rho + n);
+        sphi[k] = __ldg(phi + n);
+    }
+    for (int k = tid; k < NS; k += blockDim.x) {
+        int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
+        stype[k] = __ldg(type + node_of(p, x0 - 1 + lx, y0 - 1 + ly, z0 - HZ1 + lz));
+    }
+    __syncthreads();
+
+    // Stage B: Q = rho c_s^2 I - P and mu_phi at every fluid node of the tile + halo 1
+    for (int k = tid; k < NS; k += blockDim.x) {
+        int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
+        if (stype[k] & TLB_SOLID) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) sQ[c][k] = 0.f;
+            smu[k] = 0.f;
+            continue;
+        }
+        Thermo<D> t = node_thermo<D, RX, RY>(p, srho, sphi, lx + 1, ly + 1, lz + (D == 3 ? 1 : 0));
+        float r0 = srho[(lx + 1) + RX * ((ly + 1) + RY * (lz + (D == 3 ? 1 : 0)))];
+        if (D == 2) {
+            sQ[0][k] = r0 * (1.0f / 3.0f) - t.P[0];
+            sQ[1][k] = r0 * (1.0f / 3.0f) - t.P[1];
+            sQ[2][k] = -t.P[3];
+        } else {
+            sQ[0][k] = r0 * (1.0f / 3.0f) - t.P[0];
+            sQ[1][k] = r0 * (1.0f / 3.0f) - t.P[1];
+            sQ[2][k] = r0 * (1.0f / 3.0f) - t.P[2];
+            sQ[3][k] = -t.P[3];
+            sQ[4][k] = -t.P[4];
+            sQ[5][k] = -t.P[5];
+        }
+        smu[k] = t.mup;
+    }
+    __syncthreads();
+
+    // Stage C: one node per thread
+    const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
+    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+    if (x >= p.nx || y >= p.ny || z >= p.nz) return;
+    const int sx = tx + 1, sy = ty + 1, sz = tz + HZ1;
+    const int sc = sx + SX * (sy + SY * sz);
+    const uint8_t tc = stype[sc];
+    const long long n = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
+    if (tc & TLB_SOLID) return;
+    const float r = srho[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
+    const float ph = sphi[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
+
+    // force F = div(rho c_s^2 I - P) with the wall rules (Sec. IV)
+    bool wall[3] = {(tc & TLB_WALLX) != 0, (tc & TLB_WALLY) != 0, (tc & TLB_WALLZ) != 0};
+    float F[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int gdir = 0; gdir < D; ++gdir) {
+        if (wall[gdir]) {
+            // one-sided along a wall axis: fluid-side differences, doubled
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (cc<D>(i, gdir) == 0) continue;
+                int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
+                if (stype[m] & TLB_SOLID) continue;
+                float wc = 6.0f * wt<D>(i) * (float)cc<D>(i, gdir);
+#pragma unroll
+                for (int a = 0; a < D; ++a) F[a] += wc * (sQ[qcomp<D>(a, gdir)][m] - sQ[qcomp<D>(a, gdir)][sc]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (cc<D>(i, gdir) == 0) continue;
+                int cx = cc<D>(i, 0), cy = cc<D>(i, 1), cz = cc<D>(i, 2);
+                int m = (sx + cx) + SX * ((sy + cy) + SY * (sz + cz));
+                if (stype[m] & TLB_SOLID) {
+                    // mirror image across the wall axes, else the node itself
+                    if (wall[0]) cx = -cx;
+                    if (wall[1]) cy = -cy;
+                    if (D == 3 && wall[2]) cz = -cz;
+                    int mm = (sx + cx) + SX * ((sy + cy) + SY * (sz + cz));
+                    m = (stype[mm] & TLB_SOLID) ? sc : mm;
+                }
+                float wc = 3.0f * wt<D>(i) * (float)cc<D>(i, gdir);
+#pragma unroll
+                for (int a = 0; a < D; ++a) F[a] += wc * sQ[qcomp<D>(a, gdir)][m];
+            }
+        }
+    }
+    // wetting force of method 1 (Eq. forceBC) on fluid nodes off the first layer
+    if (p.wetting == TLB_WET_FORCE && !(tc & TLB_FIRST) && (p.kw_rho != 0.f || p.kw_phi != 0.f)) {
+        float rrel = (r - p.rho_g) * p.inv_drho;
+        float amp = rrel * (p.kw_rho + ph * p.inv_chi * p.kw_phi);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
+            if (!(stype[m] & TLB_FIRST)) continue;
+#pragma unroll
+            for (int a = 0; a < D; ++a) F[a] += amp * wt<D>(i) * (float)cc<D>(i, a);
+        }
+    }
+    const float mup = smu[sc];
+
+    if (MODE == MODE_AUX) {
+        Thermo<D> t = node_thermo<D, RX, RY>(p, srho, sphi, sx + 1, sy + 1, sz + (D == 3 ? 1 : 0));
+        if (aux.p0) aux.p0[n] = t.b.p0;
+        if (aux.mur) aux.mur[n] = t.mur;
+        if (aux.mup) aux.mup[n] = t.mup;
+        for (int a = 0; a < 3; ++a)
+            if (aux.F[a]) aux.F[a][n] = (a < D) ? F[a] : 0.f;
+        for (int k = 0; k < 6; ++k)
+            if (aux.P[k]) aux.P[k][n] = t.P[k];
+        return;
+    }
+
+    const float inv_r = 1.0f / r;
+    if (MODE == MODE_INIT) {
+        // f = f^eq(rho, v - F/(2 rho)), g = g^eq(phi, v, mu_phi) at the node itself
+        float v[3] = {0.f, 0.f, 0.f}, ub[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            v[a] = u_init ? u_init[(long long)a * p.N + n] : 0.f;
+            ub[a] = v[a] - 0.5f * F[a] * inv_r;
+        }
+        Fac fu[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) fu[a] = eq_factors(ub[a]);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float e = r;
+#pragma unroll
+            for (int a = 0; a < D; ++a) e *= fac_of(fu[a], cc<D>(i, a));
+            f_out[(long long)i * p.N + n] = e - wt<D>(i);
+        }
+        float v2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v2 += v[a] * v[a];
+        float gsum = 0.f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            float cv = 0.f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) cv += (float)cc<D>(i, a) * v[a];
+            float ge = wt<D>(i) * (3.0f * p.Gamma * mup + 3.0f * ph * cv + 4.5f * ph * cv * cv - 1.5f * ph * v2);
+            gsum += ge;
+            GIO<GT>::st(g_out, (long long)i * p.N + n, ge, p.g_scale);
+        }
+        GIO<GT>::st(g_out, n, ph - gsum, p.g_scale);
+        return;
+    }
+
+    // ---- ELBM collision of f (Eqs. ELBMequation, ELBMForcingExactDiff, EntropyEquation) ----
+    float fp[Q], dl[Q];
+    float j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float fi = __ldg(f_in + (long long)i * p.N + n);   // f_i - w_i
+        fp[i] = fi;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (cc<D>(i, a) != 0) j[a] += (float)cc<D>(i, a) * fi;
+    }
+    float u[3], ud[3], v[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        u[a] = j[a] * inv_r;
+        float du = F[a] * inv_r;          // delta u = F dt / rho
+        ud[a] = u[a] + du;
+        v[a] = u[a] + 0.5f * du;          // fluid velocity
+    }
+    Fac fu[3], fd[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        fu[a] = eq_factors(u[a]);
+        fd[a] = eq_factors(ud[a]);
+    }
+    bool bad = !(r > 0.f);
+    float xmax = 0.f, amax = 3.0e38f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float e = r, ed = r;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            e *= fac_of(fu[a], cc<D>(i, a));
+            ed *= fac_of(fd[a], cc<D>(i, a));
+        }
+        float fi = fp[i] + wt<D>(i);
+        float mirror = fi + (ed - e);     // f' (Eq. mirror_state)
+        float delta = e - fi;             // f^eq(u) - f = f^eq(u + du) - f'
+        fp[i] = mirror;
+        dl[i] = delta;
+        bad |= !(mirror > 0.f);
+        xmax = fmaxf(xmax, fabsf(delta / mirror));
+        if (delta < 0.f) amax = fminf(amax, -mirror / delta);
+    }
+    float al = 2.0f;
+    if (bad) {
+        atomicOr(status, 1u);
+    } else if (xmax >= 1e-4f) {
+        al = (xmax > 1e-2f) ? alpha_solve<Q, double>(fp, dl, amax) : alpha_solve<Q, float>(fp, dl, amax);
+    }
+    const float ab = al * p.beta;
+
+    // push streaming with halfway bounce-back
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float fn = fp[i] + ab * dl[i] - wt<D>(i);
+        int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
+        if (stype[m] & TLB_SOLID)
+            f_out[(long long)opp<D>(i) * p.N + n] = fn;
+        else
+            f_out[(long long)i * p.N + node_of(p, x + cc<D>(i, 0), y + cc<D>(i, 1), z + cc<D>(i, 2))] = fn;
+    }
+
+    // ---- LBGK for g (Eq. CahnHilliardLBM) with g^eq(phi, v, mu_phi) ----
+    float v2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) v2 += v[a] * v[a];
+    float gsum = 0.f, g0 = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float gi = GIO<GT>::ld(g_in, (long long)i * p.N + n, p.g_unscale);
+        if (i == 0) { g0 = gi; continue; }
+        float cv = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) cv += (float)cc<D>(i, a) * v[a];
+        float ge = wt<D>(i) * (3.0f * p.Gamma * mup + 3.0f * ph * cv + 4.5f * ph * cv * cv - 1.5f * ph * v2);
+        gsum += ge;
+        float gn = gi + (ge - gi) * p.inv_tau_g;
+        int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
+        if (stype[m] & TLB_SOLID)
+            GIO<GT>::st(g_out, (long long)opp<D>(i) * p.N + n, gn, p.g_scale);
+        else
+            GIO<GT>::st(g_out, (long long)i * p.N + node_of(p, x + cc<D>(i, 0), y + cc<D>(i, 1), z + cc<D>(i, 2)), gn,
+                        p.g_scale);
+    }
+    {
+        float ge0 = ph - gsum;
+        GIO<GT>::st(g_out, n, g0 + (ge0 - g0) * p.inv_tau_g, p.g_scale);
+    }
+}
+
+template <int D, typename GT, int MODE>
+__global__ void __launch_bounds__(256) step_kernel(DevParams p, const float *__restrict__ f_in, float *__restrict__ f_out,
+                                                   const void *g_in, void *g_out, const float *__restrict__ rho,
+                                                   const float *__restrict__ phi, const uint8_t *__restrict__ type,
+                                                   unsigned *status, const float *__restrict__ u_init, AuxOut aux)
+{
+    int x0 = blockIdx.x * Tile<D>::X, y0 = blockIdx.y * Tile<D>::Y, z0 = blockIdx.z * Tile<D>::Z;
+    step_tile<D, GT, MODE>(p, f_in, f_out, g_in, g_out, rho, phi, type, status, x0, y0, z0, u_init, aux);
+}
+
+template <int D, typename GT>
+__global__ void __launch_bounds__(256) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
+{
+    int4 t = tiles[blockIdx.x];
+    const BatchEntry &e = E[t.x];
+    AuxOut none = {};
+    step_tile<D, GT, MODE_STEP>(e.p, e.f_in, e.f_out, e.g_in, e.g_out, e.rho, e.phi, e.type, e.status, t.y, t.z, t.w,
+                                nullptr, none);
+}
+
+// ---------------------------------------------------------------------------
+// fields: bare velocity u = sum f c / rho at fluid nodes
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256) fields_kernel(DevParams p, const float *__restrict__ f, const float *__restrict__ rho,
+                                                     const uint8_t *__restrict__ type, float *u)
+{
+    constexpr int Q = Lat<D>::Q;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < p.N; n += (long long)gridDim.x * blockDim.x) {
+        float j[3] = {0.f, 0.f, 0.f};
+        bool solid = type[n] & TLB_SOLID;
+        if (!solid) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                float fi = f[(long long)i * p.N + n];
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    if (cc<D>(i, a) != 0) j[a] += (float)cc<D>(i, a) * fi;
+            }
+        }
+        float ir = solid ? 0.f : 1.0f / rho[n];
+#pragma unroll
+        for (int a = 0; a < D; ++a) u[(long long)a * p.N + n] = j[a] * ir;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 diagnostics: per-block partial sums (fixed order), then one block.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256) diag_kernel(DevParams p, const float *__restrict__ f, const float *__restrict__ rho,
+                                                   const float *__restrict__ phi, const uint8_t *__restrict__ type,
+                                                   double *partials)
+{
+    constexpr int Q = Lat<D>::Q;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < p.N; n += (long long)gridDim.x * blockDim.x) {
+        if (type[n] & TLB_SOLID) continue;
+        double r = rho[n], ph = phi[n];
+        double C1 = (r - (double)p.rho_l) / ((double)p.rho_g - (double)p.rho_l);
+        s[0] += r;
+        s[1] += ph;
+        s[2] += C1;
+        s[3] += 0.5 * (1.0 + ph / (double)p.chi - C1);
+        s[4] += 0.5 * (1.0 - ph / (double)p.chi - C1);
+        double j[3] = {0, 0, 0};
+        for (int i = 1; i < Q; ++i) {
+            double fi = f[(long long)i * p.N + n];
+            for (int a = 0; a < D; ++a) j[a] += cc<D>(i, a) * fi;
+        }
+        double j2 = 0;
+        for (int a = 0; a < D; ++a) j2 += j[a] * j[a];
+        s[5] += 0.5 * j2 / r;
+    }
+    __shared__ double red[6][8];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 6; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        partials[(long long)blockIdx.x * 6 + threadIdx.x] = v;
+    }
+}
+
+template <int D>
+__global__ void diag_final_kernel(const double *partials, int nblocks, double *out)
+{
+    if (threadIdx.x < 6) {
+        double v = 0;
+        for (int b = 0; b < nblocks; ++b) v += partials[(long long)b * 6 + threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+}
+
+// populations <-> FP64 host-order buffers (dir 0: device -> double, 1: double -> device)
+template <int D, typename GT>
+__global__ void convert_kernel(DevParams p, float *f, void *g, double *fb, double *gb, int dir)
+{
+    constexpr int Q = Lat<D>::Q;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < p.N; n += (long long)gridDim.x * blockDim.x) {
+        for (int i = 0; i < Q; ++i) {
+            long long k = (long long)i * p.N + n;
+            if (dir == 0) {
+                fb[k] = (double)f[k] + (double)wt<D>(i);
+                gb[k] = (double)GIO<GT>::ld(g, k, p.g_unscale);
+            } else {
+                f[k] = (float)(fb[k] - (double)wt<D>(i));
+                GIO<GT>::st(g, k, (float)gb[k], p.g_scale);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+inline int grid_for(long long N, int threads)
+{
+    long long b = (N + threads - 1) / threads;
+    long long cap = 152LL * 16;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <int D>
+int Launch<D>::Q() { return Lat<D>::Q; }
+
+template <int D>
+int Launch<D>::tile_dims(int a) { return a == 0 ? Tile<D>::X : a == 1 ? Tile<D>::Y : Tile<D>::Z; }
+
+template <int D>
+void Launch<D>::moments(const DevParams &p, const DevState &s, cudaStream_t st)
+{
+    if (p.g_fp16)
+        moments_kernel<D, __half><<<grid_for(p.N, 256), 256, 0, st>>>(p, s.f[s.cur], s.g[s.cur], s.type, s.rho, s.phi);
+    else
+        moments_kernel<D, float><<<grid_for(p.N, 256), 256, 0, st>>>(p, s.f[s.cur], s.g[s.cur], s.type, s.rho, s.phi);
+}
+
+template <int D>
+void Launch<D>::ghosts(const DevParams &p, const DevState &s, cudaStream_t st)
+{
+    if (s.nghost > 0)
+        ghost_kernel<D><<<(s.nghost + 127) / 128, 128, 0, st>>>(p, s.type, s.rho, s.phi, s.ghosts, s.nghost);
+}
+
+template <int D>
+void Launch<D>::step(const DevParams &p, const DevState &s, int mode, const float *u_init, AuxOut aux, cudaStream_t st)
+{
+    dim3 grid((p.nx + Tile<D>::X - 1) / Tile<D>::X, (p.ny + Tile<D>::Y - 1) / Tile<D>::Y,
+              (p.nz + Tile<D>::Z - 1) / Tile<D>::Z);
+    dim3 block(Tile<D>::X * Tile<D>::Y * Tile<D>::Z);
+    int cur = s.cur, nxt = 1 - s.cur;
+#define TLB_LAUNCH_STEP(GT)                                                                                          \
+    do {                                                                                                             \
+        if (mode == MODE_STEP)                                                                                       \
+            step_kernel<D, GT, MODE_STEP><<<grid, block, 0, st>>>(p, s.f[cur], s.f[nxt], s.g[cur], s.g[nxt], s.rho,   \
+                                                                   s.phi, s.type, s.status, nullptr, aux);           \
+        else if (mode == MODE_INIT)                                                                                  \
+            step_kernel<D, GT, MODE_INIT><<<grid, block, 0, st>>>(p, s.f[cur], s.f[cur], s.g[cur], s.g[cur], s.rho,   \
+                                                                   s.phi, s.type, s.status, u_init, aux);            \
+        else                                                                                                         \
+            step_kernel<D, GT, MODE_AUX><<<grid, block, 0, st>>>(p, s.f[cur], s.f[cur], s.g[cur], s.g[cur], s.rho,    \
+                                                                  s.phi, s.type, s.status, nullptr, aux);            \
+    } while (0)
+    if (p.g_fp16) TLB_LAUNCH_STEP(__half);
+    else TLB_LAUNCH_STEP(float);
+#undef TLB_LAUNCH_STEP
+}
+
+template <int D>
+void Launch<D>::fields(const DevParams &p, const DevState &s, float *u_out, cudaStream_t st)
+{
+    fields_kernel<D><<<grid_for(p.N, 256), 256, 0, st>>>(p, s.f[s.cur], s.rho, s.type, u_out);
+}
+
+template <int D>
+int Launch<D>::diag_blocks(const DevParams &p) { return grid_for(p.N, 256) < 1024 ? grid_for(p.N, 256) : 1024; }
+
+template <int D>
+void Launch<D>::diagnostics(const DevParams &p, const DevState &s, double *partials, int nblocks, double *out,
+                            cudaStream_t st)
+{
+    diag_kernel<D><<<nblocks, 256, 0, st>>>(p, s.f[s.cur], s.rho, s.phi, s.type, partials);
+    diag_final_kernel<D><<<1, 32, 0, st>>>(partials, nblocks, out);
+}
+
+template <int D>
+void Launch<D>::convert_pop(const DevParams &p, const DevState &s, int dir, double *fbuf, double *gbuf, cudaStream_t st)
+{
+    if (p.g_fp16)
+        convert_kernel<D, __half><<<grid_for(p.N, 256), 256, 0, st>>>(p, s.f[s.cur], s.g[s.cur], fbuf, gbuf, dir);
+    else
+        convert_kernel<D, float><<<grid_for(p.N, 256), 256, 0, st>>>(p, s.f[s.cur], s.g[s.cur], fbuf, gbuf, dir);
+}
+
+template <int D>
+void Launch<D>::moments_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, cudaStream_t st)
+{
+    if (ntiles > 0)
+        moments_batch_kernel<D, float><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
+}
+
+template <int D>
+void Launch<D>::step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, cudaStream_t st)
+{
+    if (ntiles > 0)
+        step_batch_kernel<D, float><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
+}
+
+template <int D>
+void ghosts_batch_launch(const BatchEntry *entries, const int2 *gl, int n, cudaStream_t st)
+{
+    if (n > 0) ghost_batch_kernel<D><<<(n + 127) / 128, 128, 0, st>>>(entries, gl, n);
+}
+
+}  // namespace tlb

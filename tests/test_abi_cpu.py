@@ -1,0 +1,67 @@
+"""CPU-side checks of the C ABI library: it loads without a GPU and exports
+every entry point that include/tlb.h declares; host-only calls behave."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1904_06881_gb300 import build, tlb
+
+    build.build()
+    return tlb.lib()
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "tlb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tlb_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    from paper_1904_06881_gb300 import tlb
+
+    assert declared_entry_points() == sorted(tlb.ENTRY_POINTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_entry_points() if not hasattr(L, n)]
+    assert not missing
+
+
+def test_host_only_calls(L):
+    from paper_1904_06881_gb300 import tlb
+
+    assert L.tlb_strerror(-6) == b"non-positive density or population"
+    maj, mnr, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert L.tlb_version(ctypes.byref(maj), ctypes.byref(mnr), ctypes.byref(sm)) == 0 and sm.value == 103
+    p = tlb.tlb_params_default()
+    assert p.lam[0] == 0.6 and p.kappa[1] == 1.0 and p.beta == 0.5 and p.chi == 5.0
+    c, w = tlb.tlb_lattice_directions(tlb.D3Q27)
+    assert np.isclose(w.sum(), 1.0) and (c.sum(0) == 0).all()
+    # opposite directions come in (+c, -c) pairs after the rest direction
+    assert (c[1::2] == -c[2::2]).all()
+
+
+def test_invalid_arguments_rejected_on_host(L):
+    from paper_1904_06881_gb300 import tlb
+
+    with pytest.raises(tlb.TlbError) as e:
+        tlb.tlb_create(tlb.D2Q9, 64, 64, 1, (1.0, 1e-3), (0.01, 1, 1), (0.1, 0.2, 0.1), tlb.WET_FORCE, (90, 90, 90))
+    assert e.value.code == -4          # unequal viscosities: one beta only
+    with pytest.raises(tlb.TlbError) as e:
+        tlb.tlb_create(tlb.D2Q9, 64, 64, 1, (1.0, 1e-3), (0.01, 1, 1), (1 / 6,) * 3, tlb.WET_FORCE, (60, 90, 90))
+    assert e.value.code == -5          # force wetting needs explicit kappa^w
+    with pytest.raises(tlb.TlbError) as e:
+        tlb.tlb_create(tlb.D2Q9, 2, 64, 1, (1.0, 1e-3), (0.01, 1, 1), (1 / 6,) * 3, tlb.WET_FORCE, (90, 90, 90))
+    assert e.value.code == -1
+    p = tlb.make_params(tlb.D2Q9, 64, 64, 1, wetting=tlb.WET_GEOM_INTERP, theta_deg=(10, 90, 90))
+    with pytest.raises(tlb.TlbError) as e:
+        tlb.tlb_create_ex(p)
+    assert e.value.code == -4          # geometric angles limited to [20, 160] deg
