@@ -102,10 +102,65 @@ def algorithmic_bytes(Q, N):
     return N * (16 * Q + 9)
 
 
+def measure(lat, stream, steps, warmup, flush=None, kernel_steps=None):
+    """Per-step time of whole steps (tlb_step: one CUDA graph of the step's
+    launches) and the average duration of the fused step kernel alone (launched
+    through tlb_step_phase), both with CUDA events on the lattice's stream.
+    With `flush`, a buffer larger than L2 is written before every timed step."""
+    import torch
+
+    from paper_1904_06881_gb300 import tlb
+
+    kernel_steps = kernel_steps or steps
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            if flush is not None:
+                flush.fill_(1.0)
+            tlb.tlb_step(lat.h, 1)
+        stream.synchronize()
+        tlb.tlb_sync(lat.h)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches0 = lat.launches
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            if flush is not None:
+                flush.fill_(float(k))
+            ev[k][0].record(stream)
+            tlb.tlb_step(lat.h, 1)
+            ev[k][1].record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+        launches = lat.launches - launches0
+        evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(kernel_steps)]
+        for k in range(kernel_steps):
+            if flush is not None:
+                flush.fill_(float(k))
+            tlb.tlb_step_phase(lat.h, 0)
+            tlb.tlb_step_phase(lat.h, 1)
+            evk[k][0].record(stream)
+            tlb.tlb_step_phase(lat.h, 2)
+            evk[k][1].record(stream)
+        stream.synchronize()
+        tlb.tlb_sync(lat.h)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    kern_ms = sum(a.elapsed_time(b) for a, b in evk) / kernel_steps
+    return step_ms, kern_ms, launches, wall
+
+
+def roofline(Q, N, kern_ms, peak, peak_kind, kernel_name):
+    achieved = algorithmic_bytes(Q, N) / (kern_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_kind + " hbm_gbs of MEASURED_PEAKS.json",
+            "traffic": None, "kernel_ms": round(kern_ms, 5), "algorithmic_bytes_per_launch": algorithmic_bytes(Q, N)}
+
+
 def run_ours(args):
     import torch
 
     from paper_1904_06881_gb300 import tlb
+    from paper_1904_06881_gb300 import workloads as W
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -119,72 +174,48 @@ def run_ours(args):
     tlb.tlb_set_stream(lat.h, stream.cuda_stream)
     N, Q = lat.N, lat.Q
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    def one_step():
-        for ph in (0, 1, 2):
-            tlb.tlb_step_phase(lat.h, ph)
-
-    with torch.cuda.stream(stream):
-        for _ in range(max(args.warmup, 3)):
-            flush.fill_(1.0)
-            one_step()
-        stream.synchronize()
-        tlb.tlb_sync(lat.h)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        launches0 = lat.launches
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            t0 = time.perf_counter()
-            for k in range(args.steps):
-                flush.fill_(float(k))
-                ev[k][0].record(stream)
-                tlb.tlb_step_phase(lat.h, 0)
-                tlb.tlb_step_phase(lat.h, 1)
-                ev[k][1].record(stream)
-                tlb.tlb_step_phase(lat.h, 2)
-                ev[k][2].record(stream)
-            stream.synchronize()
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
-        launches = lat.launches - launches0
-        tlb.tlb_sync(lat.h)
-    step_ms = sum(e[0].elapsed_time(e[2]) for e in ev)
-    kern_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        step_ms, kern_ms, launches, wall = measure(lat, stream, args.steps, args.warmup, flush=flush)
     if world > 1:
         t = torch.tensor([step_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         step_ms = float(t.item())
-    ms_per_step = step_ms / args.steps
-    value = world * N / (ms_per_step * 1e-3) / 1e6
-
-    # end to end through the C ABI with host buffers: init from host, steps, fields to host
-    e2e = None
-    if rank == 0:
-        e2e = e2e_run(wl, tlb)
+    value = world * N / (step_ms * 1e-3) / 1e6
     peak, peak_kind = hbm_peak()
-    achieved = algorithmic_bytes(Q, N) / (kern_ms * 1e-3) / 1e9
     result = {
         "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["name"], "lattice": "D2Q9", "nx": wl["nx"], "ny": wl["ny"],
                    "wetting": "geometric interpolation", "angles_deg": [30, 60, 120],
-                   "density_ratio": 14.14, "l2": "256 MB buffer written between timed steps; each step timed alone",
+                   "density_ratio": 14.14, "l2": "256 MB buffer written before every timed step; steps timed alone",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "step_kernel<D2Q9> (fused stencil/collision/stream)",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": peak_kind + " (hbm_gbs)",
-                     "traffic": None, "kernel_ms": round(kern_ms, 5),
-                     "algorithmic_bytes_per_launch": algorithmic_bytes(Q, N)},
+        "roofline": roofline(Q, N, kern_ms, peak, peak_kind, "step_kernel<D2Q9> (stencils, force, collision, stream)"),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "host_wall_s": round(wall, 4),
     }
-    if e2e:
-        result["e2e"] = e2e
+    lat.close()
+    del flush
+    if rank == 0:
+        result["e2e"] = e2e_run(wl, tlb)
+    if not args.no_large:
+        # the D3Q27 192x192x128 lubricated substrate: state (2.1 GB) far larger than L2
+        big = W.c2_lubricated(kw_rho=0.02)
+        lb = tlb.lattice_from_workload(big)
+        tlb.tlb_set_stream(lb.h, stream.cuda_stream)
+        with ClockSampler(local) as clk2:
+            bms, bkms, blaunch, _ = measure(lb, stream, max(args.steps // 10, 10), 3, flush=None)
+        result["large_lattice"] = {
+            "workload": big["name"], "value": round(world * lb.N / (bms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+            "ms_per_step": round(bms, 4), "gpu_launches": int(blaunch), "clocks": clk2.summary(),
+            "l2": "state 2.1 GB, larger than L2; no flush",
+            "roofline": roofline(lb.Q, lb.N, bkms, peak, peak_kind,
+                                 "step_kernel<D3Q27> (stencils, force, collision, stream)")}
+        lb.close()
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
     if world > 1:
@@ -271,6 +302,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the D3Q27 192x192x128 measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     res = run_reference(args) if args.impl == "reference" else run_ours(args)

@@ -362,7 +362,19 @@ struct tlb_ctx {
     long long steps = 0;
     long long launches = 0;
     int sticky = TLB_OK;
+    // one CUDA graph per buffer parity holding the three launches of a step
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
 };
+
+static void drop_graphs(tlb_ctx *c)
+{
+    for (int k = 0; k < 2; ++k)
+        if (c->gexec[k]) {
+            cudaGraphExecDestroy(c->gexec[k]);
+            c->gexec[k] = nullptr;
+        }
+}
 
 static int Qof(int lattice) { return lattice == TLB_D3Q27 ? 27 : 9; }
 static int Dof(int lattice) { return lattice == TLB_D3Q27 ? 3 : 2; }
@@ -488,6 +500,8 @@ extern "C" void tlb_destroy(tlb_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     dev_free_all(c->owned);
     delete c;
 }
@@ -558,6 +572,7 @@ extern "C" int tlb_set_solid(tlb_ctx *c, const uint8_t *mask)
                 t[n] = v;
             }
     c->type_host = t;
+    drop_graphs(c);
     CUDA_TRY(cudaMemcpyAsync(c->s.type, t.data(), N, cudaMemcpyHostToDevice, c->stream));
     size_t ng = c->ghost_host.size();
     if (ng > c->ghosts_cap) {
@@ -646,22 +661,47 @@ extern "C" int tlb_init_fields(tlb_ctx *c, const double *rho, const double *phi,
     return TLB_OK;
 }
 
-static void issue_step(tlb_ctx *c)
+static void issue_step_on(tlb_ctx *c, cudaStream_t st)
 {
     AuxOut none = {};
-    DISPATCH(c, moments(c->dp, c->s, c->stream));
-    DISPATCH(c, ghosts(c->dp, c->s, c->stream));
-    DISPATCH(c, step(c->dp, c->s, MODE_STEP, nullptr, none, c->stream));
-    c->s.cur ^= 1;
-    c->steps += 1;
-    c->launches += (c->s.nghost > 0) ? 3 : 2;
+    DISPATCH(c, moments(c->dp, c->s, st));
+    DISPATCH(c, ghosts(c->dp, c->s, st));
+    DISPATCH(c, step(c->dp, c->s, MODE_STEP, nullptr, none, st));
+}
+
+// Capture the three launches of a step for the current buffer parity.
+static int capture_step(tlb_ctx *c)
+{
+    int par = c->s.cur;
+    if (c->gexec[par]) return TLB_OK;
+    if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    issue_step_on(c, c->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) return fail(TLB_E_CUDA, "step capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec[par], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec[par] = nullptr;
+        return fail(TLB_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return TLB_OK;
 }
 
 extern "C" int tlb_step(tlb_ctx *c, int nsteps)
 {
     if (!c) return fail(TLB_E_INVAL, "null context");
     if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
-    for (int k = 0; k < nsteps; ++k) issue_step(c);
+    int per = (c->s.nghost > 0) ? 3 : 2;
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = capture_step(c);
+        if (rc) return rc;
+        CUDA_TRY(cudaGraphLaunch(c->gexec[c->s.cur], c->stream));
+        c->s.cur ^= 1;
+        c->steps += 1;
+        c->launches += per;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(TLB_E_CUDA, "step launch: %s", cudaGetErrorString(e));
     return c->sticky;

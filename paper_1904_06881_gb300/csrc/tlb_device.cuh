@@ -187,14 +187,14 @@ __device__ __forceinline__ float alpha_solve(const float (&fp)[Q], const float (
     }
     float al = 2.0f;
     if (!(al > lo && al < hi)) al = 0.5f * (lo + hi);
-    for (int it = 0; it < 24; ++it) {
+    for (int it = 0; it < 12; ++it) {
         Acc h = hval(al, dh);
         if (h > (Acc)0) hi = al; else lo = al;
         float nxt = (dh != (Acc)0) ? (float)((Acc)al - h / dh) : 0.5f * (lo + hi);
         if (!(nxt > lo && nxt < hi)) nxt = 0.5f * (lo + hi);
-        if (fabsf(nxt - al) <= 2e-7f * al) { al = nxt; break; }
+        bool done = fabsf(nxt - al) <= 1e-6f * al;
         al = nxt;
-        if (hi - lo <= 4e-7f * hi) break;
+        if (done || hi - lo <= 2e-6f * hi) break;
     }
     return al;
 }

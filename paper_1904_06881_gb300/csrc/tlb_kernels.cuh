@@ -394,11 +394,12 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
 
     // ---- ELBM collision of f (Eqs. ELBMequation, ELBMForcingExactDiff, EntropyEquation) ----
+    // fp holds f~ = f - w on load and the mirror state f' after the second pass.
     float fp[Q], dl[Q];
     float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float fi = __ldg(f_in + (long long)i * p.N + n);   // f_i - w_i
+        float fi = __ldg(f_in + (long long)i * p.N + n);
         fp[i] = fi;
 #pragma unroll
         for (int a = 0; a < D; ++a)
@@ -418,24 +419,60 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         fu[a] = eq_factors(u[a]);
         fd[a] = eq_factors(ud[a]);
     }
-    bool bad = !(r > 0.f);
-    float xmax = 0.f, amax = 3.0e38f;
+    // The relaxation D_i = f^eq_i(u) - f_i carries no mass or momentum and the
+    // forcing term F_i = f^eq_i(u+du) - f^eq_i(u) carries mass 0 and momentum F.
+    // First pass: the FP32 residuals of those balances over i >= 1; the rest
+    // population closes the mass balance and the +-axis pairs the momentum
+    // balance, so the update conserves mass and momentum to rounding.
+    float rdl = 0.f, rF = 0.f, mdl[3] = {0.f, 0.f, 0.f}, mF[3] = {F[0], F[1], F[2]};
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
         float e = r, ed = r;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             e *= fac_of(fu[a], cc<D>(i, a));
             ed *= fac_of(fd[a], cc<D>(i, a));
         }
-        float fi = fp[i] + wt<D>(i);
-        float mirror = fi + (ed - e);     // f' (Eq. mirror_state)
-        float delta = e - fi;             // f^eq(u) - f = f^eq(u + du) - f'
-        fp[i] = mirror;
-        dl[i] = delta;
-        bad |= !(mirror > 0.f);
-        xmax = fmaxf(xmax, fabsf(delta / mirror));
-        if (delta < 0.f) amax = fminf(amax, -mirror / delta);
+        float di = (e - wt<D>(i)) - fp[i];
+        float Fi = ed - e;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (cc<D>(i, a) != 0) {
+                mdl[a] += (float)cc<D>(i, a) * di;
+                mF[a] -= (float)cc<D>(i, a) * Fi;
+            }
+    }
+    // second pass: D_i, F_i with the pair corrections, f' = f + F_i
+    bool bad = !(r > 0.f);
+    float xmax = 0.f, amax = 3.0e38f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        float e = r, ed = r;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            e *= fac_of(fu[a], cc<D>(i, a));
+            ed *= fac_of(fd[a], cc<D>(i, a));
+        }
+        float di = (e - wt<D>(i)) - fp[i];
+        float Fi = ed - e;
+        if (i <= 2 * D) {                 // axis directions: i = 2a+1 (+e_a), 2a+2 (-e_a)
+            const int a = (i - 1) / 2;
+            const float sg = ((i - 1) % 2 == 0) ? 1.0f : -1.0f;
+            di -= sg * 0.5f * mdl[a];
+            Fi += sg * 0.5f * mF[a];
+        }
+        rdl += di;
+        rF += Fi;
+        dl[i] = di;
+        fp[i] = (fp[i] + wt<D>(i)) + Fi;  // mirror state f' (Eq. mirror_state)
+    }
+    dl[0] = -rdl;
+    fp[0] = (fp[0] + wt<D>(0)) - rF;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        bad |= !(fp[i] > 0.f);
+        xmax = fmaxf(xmax, fabsf(dl[i] / fp[i]));
+        if (dl[i] < 0.f) amax = fminf(amax, -fp[i] / dl[i]);
     }
     float al = 2.0f;
     if (bad) {
@@ -445,10 +482,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
     const float ab = al * p.beta;
 
-    // push streaming with halfway bounce-back
+    // f_new = f' + alpha beta D (Eq. ELBMequation); push streaming with halfway bounce-back
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float fn = fp[i] + ab * dl[i] - wt<D>(i);
+        float fn = (fp[i] - wt<D>(i)) + ab * dl[i];
         int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
         if (stype[m] & TLB_SOLID)
             f_out[(long long)opp<D>(i) * p.N + n] = fn;
