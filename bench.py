@@ -268,6 +268,24 @@ def cpu_baseline(wl, seconds=15.0):
             "sample": "%d full time steps of %s (%d nodes) in %.1f s" % (n, wl["name"], N, dt)}
 
 
+def run_only(args):
+    """One lattice, timed as in the full run; for profiling under ncu."""
+    import torch
+
+    from paper_1904_06881_gb300 import tlb
+    from paper_1904_06881_gb300 import workloads as W
+
+    wl = workload() if args.only == "c1" else W.c2_lubricated(kw_rho=0.02)
+    stream = torch.cuda.Stream()
+    lat = tlb.lattice_from_workload(wl)
+    tlb.tlb_set_stream(lat.h, stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if args.only == "c1" else None
+    step_ms, kern_ms, launches, _ = measure(lat, stream, args.steps, args.warmup, flush=flush)
+    return {"workload": wl["name"], "value": round(lat.N / (step_ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+            "ms_per_step": round(step_ms, 5), "kernel_ms": round(kern_ms, 5), "gpu_launches": int(launches),
+            "note": "profiling run; not a benchmark line"}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -303,9 +321,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the D3Q27 192x192x128 measurement")
+    ap.add_argument("--only", choices=["c1", "c2"], help="time one lattice only (profiling runs): no e2e, no CPU baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.only:
+        res = run_only(args)
+    else:
+        res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
         print(json.dumps(res), flush=True)
 

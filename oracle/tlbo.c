@@ -337,8 +337,10 @@ static double alpha_t(const lat_t *L, const double *fp, const double *delta, int
         if (h > 0.0) hi = al; else lo = al;
         if (fabs(h) <= tol_h) break;
         double nxt = (dh != 0.0) ? al - h / dh : 0.5 * (lo + hi);
-        if (!(nxt > lo && nxt < hi)) nxt = 0.5 * (lo + hi);
+        /* a Newton step below the resolution of alpha is the root (checked
+         * before the bracket test, which a converged step can touch) */
         if (fabs(nxt - al) <= 1e-14 * al) { al = nxt; break; }
+        if (!(nxt > lo && nxt < hi)) nxt = 0.5 * (lo + hi);
         al = nxt;
         if (hi - lo <= 1e-15 * hi) break;
     }

@@ -187,14 +187,21 @@ __device__ __forceinline__ float alpha_solve(const float (&fp)[Q], const float (
     }
     float al = 2.0f;
     if (!(al > lo && al < hi)) al = 0.5f * (lo + hi);
-    for (int it = 0; it < 12; ++it) {
+    for (int it = 0; it < 16; ++it) {
         Acc h = hval(al, dh);
         if (h > (Acc)0) hi = al; else lo = al;
-        float nxt = (dh != (Acc)0) ? (float)((Acc)al - h / dh) : 0.5f * (lo + hi);
-        if (!(nxt > lo && nxt < hi)) nxt = 0.5f * (lo + hi);
-        bool done = fabsf(nxt - al) <= 1e-6f * al;
-        al = nxt;
-        if (done || hi - lo <= 2e-6f * hi) break;
+        if (dh > (Acc)0) {
+            float step = (float)(h / dh);
+            if (fabsf(step) <= 1e-6f * al) {   // converged: accept the last Newton step
+                al -= step;
+                break;
+            }
+            float nxt = al - step;
+            al = (nxt > lo && nxt < hi) ? nxt : 0.5f * (lo + hi);
+        } else {
+            al = 0.5f * (lo + hi);
+        }
+        if (hi - lo <= 2e-6f * hi) break;
     }
     return al;
 }
