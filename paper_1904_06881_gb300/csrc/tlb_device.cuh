@@ -151,41 +151,54 @@ __device__ __forceinline__ float phi_ent(float y)
     return (1.0f + y) * log1pf(y) - y;
 }
 
-// Entropic alpha: non-trivial root of H(f' + alpha D) = H(f') (Eq. EntropyEquation)
-// with D = f^eq(u) - f = f^eq(u + du) - f'.  Because ln(f^eq_i(u+du)/w_i) is
-// affine in c_i and D has no mass or momentum,
-//   h(alpha) = alpha S1 + sum_i f'_i phi(alpha x_i),  x_i = D_i/f'_i,
-//   S1 = sum_i D_i ln(1 - D_i/f^eq_i(u+du)),
-// a form with no cancellation between O(1) entropies.  Newton from alpha = 2,
-// bracketed by [1, alpha_max) where alpha_max keeps every population
-// positive.  Near the interface (max |x| > 1e-2) the sums and the Newton ratio
-// are accumulated in FP64.
-template <int Q, typename Acc>
-__device__ __forceinline__ float alpha_solve(const float (&fp)[Q], const float (&dl)[Q], float amax)
+// Entropic alpha: the non-trivial root of H(f' + alpha D) = H(f')
+// (Eq. EntropyEquation) with D = f^eq(u) - f = f^eq(u + du) - f'.  With
+// x_i = D_i / f'_i, and because D carries no mass or momentum while
+// ln(f^eq_i(u+du)/w_i) is affine in c_i,
+//   h(alpha) = sum_i f'_i [ phi(alpha x_i) - alpha x_i ln(1 + x_i) ],
+//   h'(alpha) = sum_i D_i [ ln(1 + alpha x_i) - ln(1 + x_i) ],
+// which involves no difference of O(1) entropies.  Expanding in x with the
+// moments a_k = sum_i f'_i x_i^k gives the near-equilibrium root
+//   alpha = 2 + (a_3 - 2 a_4) / (3 a_2) + O(x^2),
+// used as is below max|x| = 3e-3 (its effect on f is below 1e-7 there) and as
+// the start of Newton's method, bracketed by [1, alpha_max), above it.  Near
+// the interface (max |x| > 1e-2) the Newton sums and ratio are FP64.
+template <int Q>
+__device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&dl)[Q])
 {
-    Acc S1 = 0;
+    float a2 = 0.f, a3 = 0.f, a4 = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float feqd = fp[i] + dl[i];
-        S1 += (Acc)(dl[i] * log1pf(-dl[i] / feqd));
+        float x = dl[i] / fp[i];
+        float fx2 = fp[i] * x * x;
+        a2 += fx2;
+        a3 += fx2 * x;
+        a4 += fx2 * x * x;
     }
-    float lo = 1.0f, hi = amax * (1.0f - 1e-6f);
-    auto hval = [&](float al, Acc &dh) {
-        Acc h = (Acc)al * S1;
-        dh = S1;
+    return a2 > 0.f ? 2.0f + (a3 - 2.0f * a4) / (3.0f * a2) : 2.0f;
+}
+
+template <int Q, typename Acc>
+__device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float (&dl)[Q], float amax, float al)
+{
+    float L[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) L[i] = log1pf(dl[i] / fp[i]);
+    auto hval = [&](float a, Acc &dh) {
+        Acc h = 0;
+        dh = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            float y = al * (dl[i] / fp[i]);
-            h += (Acc)(fp[i] * phi_ent(y));
-            dh += (Acc)(dl[i] * log1pf(y));
+            float x = dl[i] / fp[i];
+            float y = a * x;
+            h += (Acc)(fp[i] * (phi_ent(y) - y * L[i]));
+            dh += (Acc)(dl[i] * (log1pf(y) - L[i]));
         }
         return h;
     };
+    float lo = 1.0f, hi = amax * (1.0f - 1e-6f);
     Acc dh;
-    if (hi < 4.0f) {
-        if (hval(hi, dh) < (Acc)0) return hi;       // no root below the positivity bound
-    }
-    float al = 2.0f;
+    if (hi < 4.0f && hval(hi, dh) < (Acc)0) return hi;      // no root below the positivity bound
     if (!(al > lo && al < hi)) al = 0.5f * (lo + hi);
     for (int it = 0; it < 16; ++it) {
         Acc h = hval(al, dh);

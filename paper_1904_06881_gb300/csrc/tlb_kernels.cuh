@@ -292,6 +292,16 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     const uint8_t tc = stype[sc];
     const long long n = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
     if (tc & TLB_SOLID) return;
+    // periodic neighbour coordinates, for the push-streaming store addresses
+    const int xm = x == 0 ? p.nx - 1 : x - 1, xq = x == p.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? p.ny - 1 : y - 1, yq = y == p.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? p.nz - 1 : z - 1, zq = z == p.nz - 1 ? 0 : z + 1;
+    auto nbr = [&](int cx, int cy, int cz) -> long long {
+        int xx = cx == 0 ? x : (cx > 0 ? xq : xm);
+        int yy = cy == 0 ? y : (cy > 0 ? yq : ym);
+        int zz = cz == 0 ? z : (cz > 0 ? zq : zm);
+        return (long long)xx + (long long)p.nx * ((long long)yy + (long long)p.ny * zz);
+    };
     const float r = srho[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
     const float ph = sphi[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
 
@@ -477,8 +487,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     float al = 2.0f;
     if (bad) {
         atomicOr(status, 1u);
-    } else if (xmax >= 1e-4f) {
-        al = (xmax > 1e-2f) ? alpha_solve<Q, double>(fp, dl, amax) : alpha_solve<Q, float>(fp, dl, amax);
+    } else if (xmax >= 1e-5f) {
+        al = alpha_series<Q>(fp, dl);
+        if (xmax > 3e-3f)
+            al = (xmax > 1e-2f) ? alpha_newton<Q, double>(fp, dl, amax, al) : alpha_newton<Q, float>(fp, dl, amax, al);
     }
     const float ab = al * p.beta;
 
@@ -490,7 +502,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         if (stype[m] & TLB_SOLID)
             f_out[(long long)opp<D>(i) * p.N + n] = fn;
         else
-            f_out[(long long)i * p.N + node_of(p, x + cc<D>(i, 0), y + cc<D>(i, 1), z + cc<D>(i, 2))] = fn;
+            f_out[(long long)i * p.N + nbr(cc<D>(i, 0), cc<D>(i, 1), cc<D>(i, 2))] = fn;
     }
 
     // ---- LBGK for g (Eq. CahnHilliardLBM) with g^eq(phi, v, mu_phi) ----
@@ -512,8 +524,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         if (stype[m] & TLB_SOLID)
             GIO<GT>::st(g_out, (long long)opp<D>(i) * p.N + n, gn, p.g_scale);
         else
-            GIO<GT>::st(g_out, (long long)i * p.N + node_of(p, x + cc<D>(i, 0), y + cc<D>(i, 1), z + cc<D>(i, 2)), gn,
-                        p.g_scale);
+            GIO<GT>::st(g_out, (long long)i * p.N + nbr(cc<D>(i, 0), cc<D>(i, 1), cc<D>(i, 2)), gn, p.g_scale);
     }
     {
         float ge0 = ph - gsum;
@@ -522,7 +533,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
 }
 
 template <int D, typename GT, int MODE>
-__global__ void __launch_bounds__(256) step_kernel(DevParams p, const float *__restrict__ f_in, float *__restrict__ f_out,
+__global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_kernel(DevParams p, const float *__restrict__ f_in, float *__restrict__ f_out,
                                                    const void *g_in, void *g_out, const float *__restrict__ rho,
                                                    const float *__restrict__ phi, const uint8_t *__restrict__ type,
                                                    unsigned *status, const float *__restrict__ u_init, AuxOut aux)
@@ -532,7 +543,7 @@ __global__ void __launch_bounds__(256) step_kernel(DevParams p, const float *__r
 }
 
 template <int D, typename GT>
-__global__ void __launch_bounds__(256) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
+__global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
 {
     int4 t = tiles[blockIdx.x];
     const BatchEntry &e = E[t.x];
