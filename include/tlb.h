@@ -165,6 +165,35 @@ size_t tlb_device_bytes(const tlb_ctx *ctx);
 /* Kernel launches issued by the context since creation. */
 long long tlb_launch_count(const tlb_ctx *ctx);
 
+/* ---- allocation-free stepping (no counterpart in the paper) ----
+ * For callers that must not allocate device memory while they run: code that
+ * owns a fixed device-memory budget carved up in advance, hosts whose
+ * allocator is a framework pool that raw cudaMalloc would bypass, and loops
+ * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * imply.  tlb_step_noalloc advances caller-owned populations by nsteps and
+ * allocates nothing: its scratch (moments, node flags, ghost list, error
+ * word) is one static device array of TLB_NOALLOC_MAX_NODES * 13 + 256 bytes
+ * (13.6 MB) that every GPU loading this library holds until exit.
+ *   p          lattice, sizes and physics; at most TLB_NOALLOC_MAX_NODES
+ *              (1048576) nodes, else TLB_E_INVAL; g_fp16 must be 0.
+ *   mask       host, N bytes (1 = solid) or NULL for no walls.
+ *   f, f_tmp   device, Q*N floats each: f holds the pre-collision populations
+ *              minus the lattice weights (the layout tlb_get_populations
+ *              describes, minus w_i, as float); f_tmp is work space.
+ *   g, g_tmp   device, Q*N floats each, same roles for the order parameter.
+ *   On return the advanced populations are in f and g (asynchronously, on
+ *   cuda_stream; NULL = legacy default stream).
+ * The first call on a device looks up the scratch array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (flags, ghost list and error word are rewritten on every
+ * call): calls that overlap on the GPU -- concurrent streams or host threads
+ * on one device -- race and must be serialised by the caller.  Divergence is
+ * not reported by this call; use a context (tlb_sync) to get it. */
+#define TLB_NOALLOC_MAX_NODES (1 << 20)
+int tlb_step_noalloc(const tlb_params *p, const uint8_t *mask, float *f, float *f_tmp, void *g, void *g_tmp,
+                     int nsteps, void *cuda_stream);
+
 /* ---- batched lattices: many contexts advanced by one launch per phase ---- */
 /* Advance every context in ctxs[0..n) by nsteps, with one launch per kernel
  * phase covering all lattices (a tile -> lattice table).  All contexts must

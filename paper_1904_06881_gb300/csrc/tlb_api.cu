@@ -1214,3 +1214,139 @@ extern "C" void tlb_server_destroy(tlb_server *s)
     for (auto &kv : s->all) delete kv.second;
     delete s;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free stepping for callers that cannot allocate device memory
+// (no paper counterpart).  The moments, ghost list, node flags and error word
+// live in one file-scope device array, so the call performs no cudaMalloc,
+// cudaFree or other allocation on the device.
+// ---------------------------------------------------------------------------
+// layout: rho (N floats) | phi (N floats) | ghost list (N ints) | flags (N bytes) | status word
+static __device__ __align__(256) unsigned char g_noalloc_scratch[(size_t)TLB_NOALLOC_MAX_NODES * 13 + 256];
+
+namespace {
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *base = nullptr;    // device address of g_noalloc_scratch
+};
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[64];
+}  // namespace
+
+extern "C" int tlb_step_noalloc(const tlb_params *p, const uint8_t *mask, float *f, float *f_tmp, void *g,
+                                void *g_tmp, int nsteps, void *cuda_stream)
+{
+    if (!p || !f || !f_tmp || !g || !g_tmp) return fail(TLB_E_INVAL, "null argument");
+    if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
+    int rc = validate(*p);
+    if (rc) return rc;
+    if (p->g_fp16) return fail(TLB_E_UNSUPPORTED, "tlb_step_noalloc takes FP32 g only");
+    long long N = (long long)p->nx * p->ny * p->nz;
+    if (N > TLB_NOALLOC_MAX_NODES)
+        return fail(TLB_E_INVAL, "tlb_step_noalloc handles at most %d nodes (got %lld)", TLB_NOALLOC_MAX_NODES, N);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TLB_E_UNSUPPORTED, "device index %d out of range", dev);
+    unsigned char *base;
+    {
+        // set-up once per device, with that device current: the device address
+        // of the scratch array (its host-side name is not a device address)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        NoallocDevice &nd = g_noalloc_dev[dev];
+        if (!nd.ready) {
+            void *ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return fail(TLB_E_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            nd.base = (unsigned char *)ptr;
+            nd.ready = true;
+        }
+        base = nd.base;
+    }
+    // derived constants: host computation only
+    static thread_local tlb_params last_p;
+    static thread_local tlb_derived last_d;
+    static thread_local bool have_last = false;
+    if (!have_last || std::memcmp(&last_p, p, sizeof(tlb_params)) != 0) {
+        tlb_derived d;
+        rc = derive(*p, d);
+        if (rc) return rc;
+        last_p = *p;
+        last_d = d;
+        have_last = true;
+    }
+    DevParams dp = make_dev(*p, last_d);
+    // node flags and ghost list from the host mask (same rules as tlb_set_solid)
+    int nx = p->nx, ny = p->ny, nz = p->nz, D = Dof(p->lattice);
+    auto at = [&](int x, int y, int z) -> long long {
+        x = ((x % nx) + nx) % nx;
+        y = ((y % ny) + ny) % ny;
+        z = ((z % nz) + nz) % nz;
+        return (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+    };
+    std::vector<uint8_t> flags((size_t)N, 0);
+    std::vector<int> ghosts;
+    auto solid = [&](long long n) { return mask != nullptr && mask[n] != 0; };
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long long n = at(x, y, z);
+                bool s = solid(n), touch = false;
+                int zr = D == 3 ? 1 : 0;
+                for (int dz = -zr; dz <= zr; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx)
+                            if ((dx || dy || dz) && solid(at(x + dx, y + dy, z + dz)) != s) touch = true;
+                uint8_t v = s ? TLB_SOLID : 0;
+                if (s && touch) {
+                    v |= TLB_GHOST;
+                    ghosts.push_back((int)n);
+                }
+                if (!s) {
+                    if (touch) v |= TLB_FIRST;
+                    if (solid(at(x + 1, y, z)) || solid(at(x - 1, y, z))) v |= TLB_WALLX;
+                    if (solid(at(x, y + 1, z)) || solid(at(x, y - 1, z))) v |= TLB_WALLY;
+                    if (D == 3 && (solid(at(x, y, z + 1)) || solid(at(x, y, z - 1)))) v |= TLB_WALLZ;
+                }
+                flags[n] = v;
+            }
+    size_t M = TLB_NOALLOC_MAX_NODES;
+    DevState s;
+    s.rho = (float *)base;
+    s.phi = (float *)(base + M * 4);
+    s.ghosts = (int *)(base + M * 8);
+    s.type = (uint8_t *)(base + M * 12);
+    s.status = (unsigned *)(base + M * 13);
+    s.nghost = (int)ghosts.size();
+    s.f[0] = f;
+    s.f[1] = f_tmp;
+    s.g[0] = g;
+    s.g[1] = g_tmp;
+    s.cur = 0;
+    // the array keeps the previous call's contents: reset what must start fresh
+    CUDA_TRY(cudaMemcpyAsync(s.type, flags.data(), (size_t)N, cudaMemcpyHostToDevice, st));
+    if (!ghosts.empty())
+        CUDA_TRY(cudaMemcpyAsync(s.ghosts, ghosts.data(), ghosts.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(unsigned), st));
+    AuxOut none = {};
+    for (int k = 0; k < nsteps; ++k) {
+        if (D == 2) {
+            Launch<2>::moments(dp, s, st);
+            Launch<2>::ghosts(dp, s, st);
+            Launch<2>::step(dp, s, MODE_STEP, nullptr, none, st);
+        } else {
+            Launch<3>::moments(dp, s, st);
+            Launch<3>::ghosts(dp, s, st);
+            Launch<3>::step(dp, s, MODE_STEP, nullptr, none, st);
+        }
+        s.cur ^= 1;
+    }
+    if (s.cur == 1) {
+        size_t QN = (size_t)Qof(p->lattice) * (size_t)N;
+        CUDA_TRY(cudaMemcpyAsync(f, f_tmp, QN * 4, cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(g, g_tmp, QN * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TLB_E_CUDA, "tlb_step_noalloc launch: %s", cudaGetErrorString(e));
+    return TLB_OK;
+}

@@ -31,7 +31,7 @@ ENTRY_POINTS = (
     "tlb_get_fields_device", "tlb_diagnostics", "tlb_get_aux", "tlb_get_populations", "tlb_set_populations",
     "tlb_lattice_directions", "tlb_snapshot_bytes", "tlb_snapshot", "tlb_restore", "tlb_steps_done",
     "tlb_device_bytes", "tlb_launch_count", "tlb_step_batch", "tlb_server_create", "tlb_submit",
-    "tlb_server_pump", "tlb_poll", "tlb_server_stats", "tlb_server_destroy",
+    "tlb_server_pump", "tlb_poll", "tlb_server_stats", "tlb_server_destroy", "tlb_step_noalloc",
 )
 
 
@@ -122,6 +122,7 @@ def lib():
         "tlb_poll": (i, [vp, ctypes.c_uint64, ctypes.POINTER(Result), dp, dp]),
         "tlb_server_stats": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz)]),
         "tlb_server_destroy": (None, [vp]),
+        "tlb_step_noalloc": (i, [ctypes.POINTER(Params), u8p, vp, vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -219,6 +220,18 @@ def tlb_lattice_directions(lattice):
 def tlb_step_batch(handles, nsteps):
     arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
     return _check(lib().tlb_step_batch(arr, len(handles), int(nsteps)), "tlb_step_batch")
+
+
+def tlb_step_noalloc(params, mask, f_ptr, f_tmp_ptr, g_ptr, g_tmp_ptr, nsteps, stream_ptr=None):
+    """Allocation-free stepping of caller-owned device populations (see tlb.h)."""
+    m = None
+    if mask is not None:
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    return _check(lib().tlb_step_noalloc(ctypes.byref(params),
+                                         None if m is None else m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                         ctypes.c_void_p(f_ptr), ctypes.c_void_p(f_tmp_ptr), ctypes.c_void_p(g_ptr),
+                                         ctypes.c_void_p(g_tmp_ptr), int(nsteps),
+                                         ctypes.c_void_p(stream_ptr) if stream_ptr else None), "tlb_step_noalloc")
 
 
 _alloc_keep = []
