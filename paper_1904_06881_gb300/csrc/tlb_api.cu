@@ -527,50 +527,66 @@ extern "C" int tlb_set_stream(tlb_ctx *c, void *stream)
     return TLB_OK;
 }
 
-static inline long long nidx(const tlb_ctx *c, int x, int y, int z)
+// Node flags and ghost list of a periodic lattice from its solid mask (NULL:
+// no walls): solid, ghost (solid with a fluid lattice neighbour), first layer
+// (fluid with a solid lattice neighbour), wall axes, and NEAR (fluid off the
+// first layer with a first-layer neighbour: where the wetting force acts).
+static void node_flags(int nx, int ny, int nz, int D, const uint8_t *mask, std::vector<uint8_t> &t,
+                       std::vector<int> &ghosts)
 {
-    int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
-    x = ((x % nx) + nx) % nx;
-    y = ((y % ny) + ny) % ny;
-    z = ((z % nz) + nz) % nz;
-    return (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+    auto at = [&](int x, int y, int z) -> long long {
+        x = ((x % nx) + nx) % nx;
+        y = ((y % ny) + ny) % ny;
+        z = ((z % nz) + nz) % nz;
+        return (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+    };
+    auto solid = [&](long long n) { return mask != nullptr && mask[n] != 0; };
+    long long N = (long long)nx * ny * nz;
+    t.assign((size_t)N, 0);
+    ghosts.clear();
+    const int zr = D == 3 ? 1 : 0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long long n = at(x, y, z);
+                bool s = solid(n), touch = false;
+                for (int dz = -zr; dz <= zr; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx)
+                            if ((dx || dy || dz) && solid(at(x + dx, y + dy, z + dz)) != s) touch = true;
+                uint8_t v = s ? TLB_SOLID : 0;
+                if (s && touch) {
+                    v |= TLB_GHOST;
+                    ghosts.push_back((int)n);
+                }
+                if (!s) {
+                    if (touch) v |= TLB_FIRST;
+                    if (solid(at(x + 1, y, z)) || solid(at(x - 1, y, z))) v |= TLB_WALLX;
+                    if (solid(at(x, y + 1, z)) || solid(at(x, y - 1, z))) v |= TLB_WALLY;
+                    if (D == 3 && (solid(at(x, y, z + 1)) || solid(at(x, y, z - 1)))) v |= TLB_WALLZ;
+                }
+                t[n] = v;
+            }
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long long n = at(x, y, z);
+                if (t[n] & (TLB_SOLID | TLB_FIRST)) continue;
+                bool near = false;
+                for (int dz = -zr; dz <= zr; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx)
+                            if ((dx || dy || dz) && (t[at(x + dx, y + dy, z + dz)] & TLB_FIRST)) near = true;
+                if (near) t[n] |= TLB_NEAR;
+            }
 }
 
 extern "C" int tlb_set_solid(tlb_ctx *c, const uint8_t *mask)
 {
     if (!c || !mask) return fail(TLB_E_INVAL, "null argument");
-    int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz, D = c->D;
     long long N = c->N;
-    std::vector<uint8_t> t(N, 0);
-    for (long long n = 0; n < N; ++n) t[n] = mask[n] ? TLB_SOLID : 0;
-    c->ghost_host.clear();
-    for (int z = 0; z < nz; ++z)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                long long n = nidx(c, x, y, z);
-                bool solid = t[n] & TLB_SOLID;
-                bool touch = false;
-                int zr = D == 3 ? 1 : 0;
-                for (int dz = -zr; dz <= zr; ++dz)
-                    for (int dy = -1; dy <= 1; ++dy)
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            if (!dx && !dy && !dz) continue;
-                            bool ns = mask[nidx(c, x + dx, y + dy, z + dz)] != 0;
-                            if (ns != solid) touch = true;
-                        }
-                uint8_t v = t[n];
-                if (solid && touch) {
-                    v |= TLB_GHOST;
-                    c->ghost_host.push_back((int)n);
-                }
-                if (!solid) {
-                    if (touch) v |= TLB_FIRST;
-                    if (mask[nidx(c, x + 1, y, z)] || mask[nidx(c, x - 1, y, z)]) v |= TLB_WALLX;
-                    if (mask[nidx(c, x, y + 1, z)] || mask[nidx(c, x, y - 1, z)]) v |= TLB_WALLY;
-                    if (D == 3 && (mask[nidx(c, x, y, z + 1)] || mask[nidx(c, x, y, z - 1)])) v |= TLB_WALLZ;
-                }
-                t[n] = v;
-            }
+    std::vector<uint8_t> t;
+    node_flags(c->p.nx, c->p.ny, c->p.nz, c->D, mask, t, c->ghost_host);
     c->type_host = t;
     drop_graphs(c);
     CUDA_TRY(cudaMemcpyAsync(c->s.type, t.data(), N, cudaMemcpyHostToDevice, c->stream));
@@ -1276,40 +1292,11 @@ extern "C" int tlb_step_noalloc(const tlb_params *p, const uint8_t *mask, float 
         have_last = true;
     }
     DevParams dp = make_dev(*p, last_d);
-    // node flags and ghost list from the host mask (same rules as tlb_set_solid)
-    int nx = p->nx, ny = p->ny, nz = p->nz, D = Dof(p->lattice);
-    auto at = [&](int x, int y, int z) -> long long {
-        x = ((x % nx) + nx) % nx;
-        y = ((y % ny) + ny) % ny;
-        z = ((z % nz) + nz) % nz;
-        return (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
-    };
-    std::vector<uint8_t> flags((size_t)N, 0);
+    // node flags and ghost list from the host mask (the rules of tlb_set_solid)
+    int D = Dof(p->lattice);
+    std::vector<uint8_t> flags;
     std::vector<int> ghosts;
-    auto solid = [&](long long n) { return mask != nullptr && mask[n] != 0; };
-    for (int z = 0; z < nz; ++z)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                long long n = at(x, y, z);
-                bool s = solid(n), touch = false;
-                int zr = D == 3 ? 1 : 0;
-                for (int dz = -zr; dz <= zr; ++dz)
-                    for (int dy = -1; dy <= 1; ++dy)
-                        for (int dx = -1; dx <= 1; ++dx)
-                            if ((dx || dy || dz) && solid(at(x + dx, y + dy, z + dz)) != s) touch = true;
-                uint8_t v = s ? TLB_SOLID : 0;
-                if (s && touch) {
-                    v |= TLB_GHOST;
-                    ghosts.push_back((int)n);
-                }
-                if (!s) {
-                    if (touch) v |= TLB_FIRST;
-                    if (solid(at(x + 1, y, z)) || solid(at(x - 1, y, z))) v |= TLB_WALLX;
-                    if (solid(at(x, y + 1, z)) || solid(at(x, y - 1, z))) v |= TLB_WALLY;
-                    if (D == 3 && (solid(at(x, y, z + 1)) || solid(at(x, y, z - 1)))) v |= TLB_WALLZ;
-                }
-                flags[n] = v;
-            }
+    node_flags(p->nx, p->ny, p->nz, D, mask, flags, ghosts);
     size_t M = TLB_NOALLOC_MAX_NODES;
     DevState s;
     s.rho = (float *)base;

@@ -156,43 +156,50 @@ __device__ __forceinline__ float phi_ent(float y)
 // x_i = D_i / f'_i, and because D carries no mass or momentum while
 // ln(f^eq_i(u+du)/w_i) is affine in c_i,
 //   h(alpha) = sum_i f'_i [ phi(alpha x_i) - alpha x_i ln(1 + x_i) ],
-//   h'(alpha) = sum_i D_i [ ln(1 + alpha x_i) - ln(1 + x_i) ],
-// which involves no difference of O(1) entropies.  Expanding in x with the
-// moments a_k = sum_i f'_i x_i^k gives the near-equilibrium root
-//   alpha = 2 + (a_3 - 2 a_4) / (3 a_2) + O(x^2),
-// used as is below max|x| = 3e-3 (its effect on f is below 1e-7 there) and as
-// the start of Newton's method, bracketed by [1, alpha_max), above it.  Near
-// the interface (max |x| > 1e-2) the Newton sums and ratio are FP64.
+//   h'(alpha) = sum_i f'_i x_i [ ln(1 + alpha x_i) - ln(1 + x_i) ],
+// which involves no difference of O(1) entropies.  Expanding h/alpha in x
+// with the moments a_k = sum_i f'_i x_i^k and solving alpha = 2 + e1 + e2 + e3
+// order by order gives
+//   e1 = a3 / (3 a2),  e2 = 2 (2 a3^2 - 3 a2 a4) / (9 a2^2),
+//   e3 = (297 a2^2 a5 - 420 a2 a3 a4 + 170 a3^3) / (270 a2^3),
+// used as is up to max|x| = 0.03 (its effect on f stays below 1e-8 there) and as
+// the start of Newton's method, bracketed by [1, alpha_max), above it; there
+// the Newton sums and ratio are FP64 (nodes at the interface).
 template <int Q>
-__device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&dl)[Q])
+__device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&x)[Q])
 {
-    float a2 = 0.f, a3 = 0.f, a4 = 0.f;
+    float a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float x = dl[i] / fp[i];
-        float fx2 = fp[i] * x * x;
+        float x2 = x[i] * x[i];
+        float fx2 = fp[i] * x2;
         a2 += fx2;
-        a3 += fx2 * x;
-        a4 += fx2 * x * x;
+        a3 += fx2 * x[i];
+        a4 += fx2 * x2;
+        a5 += fx2 * x2 * x[i];
     }
-    return a2 > 0.f ? 2.0f + (a3 - 2.0f * a4) / (3.0f * a2) : 2.0f;
+    if (!(a2 > 0.f)) return 2.0f;
+    float r = 1.0f / a2, t = a3 * r;
+    float e1 = t * (1.0f / 3.0f);
+    float e2 = (2.0f / 9.0f) * (2.0f * t * t - 3.0f * a4 * r);
+    float e3 = (297.0f * a5 * r - 420.0f * t * a4 * r + 170.0f * t * t * t) * (1.0f / 270.0f);
+    return 2.0f + e1 + e2 + e3;
 }
 
 template <int Q, typename Acc>
-__device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float (&dl)[Q], float amax, float al)
+__device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float (&x)[Q], float amax, float al)
 {
     float L[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) L[i] = log1pf(dl[i] / fp[i]);
+    for (int i = 0; i < Q; ++i) L[i] = log1pf(x[i]);
     auto hval = [&](float a, Acc &dh) {
         Acc h = 0;
         dh = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            float x = dl[i] / fp[i];
-            float y = a * x;
+            float y = a * x[i];
             h += (Acc)(fp[i] * (phi_ent(y) - y * L[i]));
-            dh += (Acc)(dl[i] * (log1pf(y) - L[i]));
+            dh += (Acc)(fp[i] * x[i] * (log1pf(y) - L[i]));
         }
         return h;
     };

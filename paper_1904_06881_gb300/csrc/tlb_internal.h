@@ -14,6 +14,7 @@ enum : uint8_t {
     TLB_WALLX = 8,      // fluid node with a solid neighbour along +-x
     TLB_WALLY = 16,     // ... along +-y
     TLB_WALLZ = 32,     // ... along +-z
+    TLB_NEAR = 64,      // fluid node off the first layer with a first-layer lattice neighbour
 };
 enum { TLB_WET_FORCE_ = 0 };
 #define TLB_WET_FORCE 0

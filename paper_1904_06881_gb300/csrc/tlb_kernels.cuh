@@ -306,43 +306,60 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     const float ph = sphi[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
 
     // force F = div(rho c_s^2 I - P) with the wall rules (Sec. IV)
-    bool wall[3] = {(tc & TLB_WALLX) != 0, (tc & TLB_WALLY) != 0, (tc & TLB_WALLZ) != 0};
     float F[3] = {0.f, 0.f, 0.f};
+    if (!(tc & TLB_FIRST)) {
+        // no solid node within one link: the isotropic stencil, one pass over the neighbours
 #pragma unroll
-    for (int gdir = 0; gdir < D; ++gdir) {
-        if (wall[gdir]) {
-            // one-sided along a wall axis: fluid-side differences, doubled
+        for (int i = 1; i < Q; ++i) {
+            const int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
+            const float w3 = 3.0f * wt<D>(i);
 #pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                if (cc<D>(i, gdir) == 0) continue;
-                int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
-                if (stype[m] & TLB_SOLID) continue;
-                float wc = 6.0f * wt<D>(i) * (float)cc<D>(i, gdir);
+            for (int a = 0; a < D; ++a) {
+                float acc = 0.f;
 #pragma unroll
-                for (int a = 0; a < D; ++a) F[a] += wc * (sQ[qcomp<D>(a, gdir)][m] - sQ[qcomp<D>(a, gdir)][sc]);
+                for (int gdir = 0; gdir < D; ++gdir)
+                    if (cc<D>(i, gdir) != 0) acc += (float)cc<D>(i, gdir) * sQ[qcomp<D>(a, gdir)][m];
+                F[a] += w3 * acc;
             }
-        } else {
+        }
+    } else {
+        bool wall[3] = {(tc & TLB_WALLX) != 0, (tc & TLB_WALLY) != 0, (tc & TLB_WALLZ) != 0};
 #pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                if (cc<D>(i, gdir) == 0) continue;
-                int cx = cc<D>(i, 0), cy = cc<D>(i, 1), cz = cc<D>(i, 2);
-                int m = (sx + cx) + SX * ((sy + cy) + SY * (sz + cz));
-                if (stype[m] & TLB_SOLID) {
-                    // mirror image across the wall axes, else the node itself
-                    if (wall[0]) cx = -cx;
-                    if (wall[1]) cy = -cy;
-                    if (D == 3 && wall[2]) cz = -cz;
-                    int mm = (sx + cx) + SX * ((sy + cy) + SY * (sz + cz));
-                    m = (stype[mm] & TLB_SOLID) ? sc : mm;
+        for (int gdir = 0; gdir < D; ++gdir) {
+            if (wall[gdir]) {
+                // one-sided along a wall axis: fluid-side differences, doubled
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    if (cc<D>(i, gdir) == 0) continue;
+                    int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
+                    if (stype[m] & TLB_SOLID) continue;
+                    float wc = 6.0f * wt<D>(i) * (float)cc<D>(i, gdir);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) F[a] += wc * (sQ[qcomp<D>(a, gdir)][m] - sQ[qcomp<D>(a, gdir)][sc]);
                 }
-                float wc = 3.0f * wt<D>(i) * (float)cc<D>(i, gdir);
+            } else {
 #pragma unroll
-                for (int a = 0; a < D; ++a) F[a] += wc * sQ[qcomp<D>(a, gdir)][m];
+                for (int i = 1; i < Q; ++i) {
+                    if (cc<D>(i, gdir) == 0) continue;
+                    int cx = cc<D>(i, 0), cy = cc<D>(i, 1), cz = cc<D>(i, 2);
+                    int m = (sx + cx) + SX * ((sy + cy) + SY * (sz + cz));
+                    if (stype[m] & TLB_SOLID) {
+                        // mirror image across the wall axes, else the node itself
+                        if (wall[0]) cx = -cx;
+                        if (wall[1]) cy = -cy;
+                        if (D == 3 && wall[2]) cz = -cz;
+                        int mm = (sx + cx) + SX * ((sy + cy) + SY * (sz + cz));
+                        m = (stype[mm] & TLB_SOLID) ? sc : mm;
+                    }
+                    float wc = 3.0f * wt<D>(i) * (float)cc<D>(i, gdir);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) F[a] += wc * sQ[qcomp<D>(a, gdir)][m];
+                }
             }
         }
     }
     // wetting force of method 1 (Eq. forceBC) on fluid nodes off the first layer
-    if (p.wetting == TLB_WET_FORCE && !(tc & TLB_FIRST) && (p.kw_rho != 0.f || p.kw_phi != 0.f)) {
+    if (p.wetting == TLB_WET_FORCE && (tc & TLB_NEAR) && (p.kw_rho != 0.f || p.kw_phi != 0.f)) {
         float rrel = (r - p.rho_g) * p.inv_drho;
         float amp = rrel * (p.kw_rho + ph * p.inv_chi * p.kw_phi);
 #pragma unroll
@@ -404,7 +421,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
 
     // ---- ELBM collision of f (Eqs. ELBMequation, ELBMForcingExactDiff, EntropyEquation) ----
-    // fp holds f~ = f - w on load and the mirror state f' after the second pass.
+    // fp holds f~ = f - w on load and the mirror state f' after the pass below.
     float fp[Q], dl[Q];
     float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -431,10 +448,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
     // The relaxation D_i = f^eq_i(u) - f_i carries no mass or momentum and the
     // forcing term F_i = f^eq_i(u+du) - f^eq_i(u) carries mass 0 and momentum F.
-    // First pass: the FP32 residuals of those balances over i >= 1; the rest
-    // population closes the mass balance and the +-axis pairs the momentum
-    // balance, so the update conserves mass and momentum to rounding.
+    // In FP32 the rest population closes the mass balances and the +-axis
+    // pairs the momentum balances, so the update conserves both to rounding.
     float rdl = 0.f, rF = 0.f, mdl[3] = {0.f, 0.f, 0.f}, mF[3] = {F[0], F[1], F[2]};
+    bool bad = !(r > 0.f);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         float e = r, ed = r;
@@ -443,61 +460,54 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             e *= fac_of(fu[a], cc<D>(i, a));
             ed *= fac_of(fd[a], cc<D>(i, a));
         }
-        float di = (e - wt<D>(i)) - fp[i];
+        float di = (e - wt<D>(i)) - fp[i];   // f^eq(u) - f = f^eq(u + du) - f'
         float Fi = ed - e;
+        rdl += di;
+        rF += Fi;
 #pragma unroll
         for (int a = 0; a < D; ++a)
             if (cc<D>(i, a) != 0) {
                 mdl[a] += (float)cc<D>(i, a) * di;
                 mF[a] -= (float)cc<D>(i, a) * Fi;
             }
-    }
-    // second pass: D_i, F_i with the pair corrections, f' = f + F_i
-    bool bad = !(r > 0.f);
-    float xmax = 0.f, amax = 3.0e38f;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        float e = r, ed = r;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            e *= fac_of(fu[a], cc<D>(i, a));
-            ed *= fac_of(fd[a], cc<D>(i, a));
-        }
-        float di = (e - wt<D>(i)) - fp[i];
-        float Fi = ed - e;
-        if (i <= 2 * D) {                 // axis directions: i = 2a+1 (+e_a), 2a+2 (-e_a)
-            const int a = (i - 1) / 2;
-            const float sg = ((i - 1) % 2 == 0) ? 1.0f : -1.0f;
-            di -= sg * 0.5f * mdl[a];
-            Fi += sg * 0.5f * mF[a];
-        }
-        rdl += di;
-        rF += Fi;
         dl[i] = di;
-        fp[i] = (fp[i] + wt<D>(i)) + Fi;  // mirror state f' (Eq. mirror_state)
+        fp[i] = (fp[i] + wt<D>(i)) + Fi;     // mirror state f' (Eq. mirror_state)
     }
     dl[0] = -rdl;
     fp[0] = (fp[0] + wt<D>(0)) - rF;
 #pragma unroll
+    for (int a = 0; a < D; ++a) {             // axis directions: i = 2a+1 (+e_a), 2a+2 (-e_a)
+        dl[2 * a + 1] -= 0.5f * mdl[a];
+        dl[2 * a + 2] += 0.5f * mdl[a];
+        fp[2 * a + 1] += 0.5f * mF[a];
+        fp[2 * a + 2] -= 0.5f * mF[a];
+    }
+    // x_i = D_i / f'_i (stored over dl), positivity bound alpha_max = 1 / max(-x_i)
+    float xmax = 0.f, xneg = 0.f;
+#pragma unroll
     for (int i = 0; i < Q; ++i) {
         bad |= !(fp[i] > 0.f);
-        xmax = fmaxf(xmax, fabsf(dl[i] / fp[i]));
-        if (dl[i] < 0.f) amax = fminf(amax, -fp[i] / dl[i]);
+        float xi = dl[i] * (1.0f / fp[i]);
+        dl[i] = xi;
+        xmax = fmaxf(xmax, fabsf(xi));
+        xneg = fmaxf(xneg, -xi);
     }
     float al = 2.0f;
     if (bad) {
         atomicOr(status, 1u);
     } else if (xmax >= 1e-5f) {
         al = alpha_series<Q>(fp, dl);
-        if (xmax > 3e-3f)
-            al = (xmax > 1e-2f) ? alpha_newton<Q, double>(fp, dl, amax, al) : alpha_newton<Q, float>(fp, dl, amax, al);
+        if (xmax > 0.03f) {
+            const float amax = xneg > 0.f ? 1.0f / xneg : 3.0e38f;
+            al = alpha_newton<Q, double>(fp, dl, amax, al);
+        }
     }
     const float ab = al * p.beta;
 
     // f_new = f' + alpha beta D (Eq. ELBMequation); push streaming with halfway bounce-back
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float fn = (fp[i] - wt<D>(i)) + ab * dl[i];
+        float fn = (fp[i] - wt<D>(i)) + ab * (dl[i] * fp[i]);
         int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
         if (stype[m] & TLB_SOLID)
             f_out[(long long)opp<D>(i) * p.N + n] = fn;
