@@ -362,6 +362,12 @@ struct tlb_ctx {
     long long steps = 0;
     long long launches = 0;
     int sticky = TLB_OK;
+    // the lattice as a batch of one: entries for both buffer parities, tile table, ghost list
+    BatchEntry *self_entries = nullptr;
+    int4 *self_tiles = nullptr;
+    int nself_tiles = 0;
+    int2 *self_glist = nullptr;
+    size_t self_glist_cap = 0;
     // one CUDA graph per buffer parity holding the three launches of a step
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaStream_t cap_stream = nullptr;
@@ -413,6 +419,14 @@ static int validate(const tlb_params &p)
     return TLB_OK;
 }
 
+#define ALLOC_LATE(field, nbytes)                                        \
+    do {                                                                 \
+        void *p_ = nullptr;                                              \
+        rc = dev_alloc(c->owned, &p_, (nbytes), &c->bytes);              \
+        if (rc) { dev_free_all(c->owned); delete c; return rc; }         \
+        field = (decltype(field))p_;                                     \
+    } while (0)
+
 extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
 {
     if (!pin || !out) return fail(TLB_E_INVAL, "null argument");
@@ -460,6 +474,35 @@ extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
     cudaMemsetAsync(c->s.rho, 0, N * 4, c->stream);
     cudaMemsetAsync(c->s.phi, 0, N * 4, c->stream);
     c->type_host.assign(N, 0);
+    {
+        // batch-of-one tables: entry per buffer parity, one tile per CTA
+        int D = c->D;
+        int TX = D == 2 ? Launch<2>::tile_dims(0) : Launch<3>::tile_dims(0);
+        int TY = D == 2 ? Launch<2>::tile_dims(1) : Launch<3>::tile_dims(1);
+        int TZ = D == 2 ? Launch<2>::tile_dims(2) : Launch<3>::tile_dims(2);
+        std::vector<int4> tiles;
+        for (int z = 0; z < c->p.nz; z += TZ)
+            for (int y = 0; y < c->p.ny; y += TY)
+                for (int x = 0; x < c->p.nx; x += TX) tiles.push_back(make_int4(0, x, y, z));
+        BatchEntry ent[2];
+        for (int par = 0; par < 2; ++par) {
+            ent[par].p = c->dp;
+            ent[par].f_in = c->s.f[par];
+            ent[par].f_out = c->s.f[1 - par];
+            ent[par].g_in = c->s.g[par];
+            ent[par].g_out = c->s.g[1 - par];
+            ent[par].rho = c->s.rho;
+            ent[par].phi = c->s.phi;
+            ent[par].type = c->s.type;
+            ent[par].status = c->s.status;
+        }
+        ALLOC_LATE(c->self_entries, sizeof(ent));
+        ALLOC_LATE(c->self_tiles, tiles.size() * sizeof(int4));
+        c->nself_tiles = (int)tiles.size();
+        cudaMemcpyAsync(c->self_entries, ent, sizeof(ent), cudaMemcpyHostToDevice, c->stream);
+        cudaMemcpyAsync(c->self_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         dev_free_all(c->owned);
@@ -601,6 +644,19 @@ extern "C" int tlb_set_solid(tlb_ctx *c, const uint8_t *mask)
     if (ng) CUDA_TRY(cudaMemcpyAsync(c->ghosts_dev, c->ghost_host.data(), ng * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     c->s.ghosts = c->ghosts_dev;
     c->s.nghost = (int)ng;
+    if (ng > c->self_glist_cap) {
+        void *ptr;
+        int rc = dev_alloc(c->owned, &ptr, ng * sizeof(int2), &c->bytes);
+        if (rc) return rc;
+        c->self_glist = (int2 *)ptr;
+        c->self_glist_cap = ng;
+    }
+    if (ng) {
+        std::vector<int2> gl(ng);
+        for (size_t k = 0; k < ng; ++k) gl[k] = make_int2(0, c->ghost_host[k]);
+        CUDA_TRY(cudaMemcpyAsync(c->self_glist, gl.data(), ng * sizeof(int2), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return TLB_OK;
 }
@@ -677,12 +733,28 @@ extern "C" int tlb_init_fields(tlb_ctx *c, const double *rho, const double *phi,
     return TLB_OK;
 }
 
+// The three launches of one step of a lattice, as a batch of one (the kernels
+// tlb_step_batch uses, so alone and batched results are bit-identical).
+static void issue_phase(tlb_ctx *c, int phase, cudaStream_t st)
+{
+    const BatchEntry *E = c->self_entries + c->s.cur;
+    int fp16 = c->p.g_fp16;
+    if (c->D == 2) {
+        if (phase == 0) Launch<2>::moments_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
+        else if (phase == 1) ghosts_batch_launch<2>(E, c->self_glist, c->s.nghost, st);
+        else Launch<2>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
+    } else {
+        if (phase == 0) Launch<3>::moments_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
+        else if (phase == 1) ghosts_batch_launch<3>(E, c->self_glist, c->s.nghost, st);
+        else Launch<3>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
+    }
+}
+
 static void issue_step_on(tlb_ctx *c, cudaStream_t st)
 {
-    AuxOut none = {};
-    DISPATCH(c, moments(c->dp, c->s, st));
-    DISPATCH(c, ghosts(c->dp, c->s, st));
-    DISPATCH(c, step(c->dp, c->s, MODE_STEP, nullptr, none, st));
+    issue_phase(c, 0, st);
+    issue_phase(c, 1, st);
+    issue_phase(c, 2, st);
 }
 
 // Capture the three launches of a step for the current buffer parity.
@@ -726,18 +798,12 @@ extern "C" int tlb_step(tlb_ctx *c, int nsteps)
 extern "C" int tlb_step_phase(tlb_ctx *c, int phase)
 {
     if (!c) return fail(TLB_E_INVAL, "null context");
-    AuxOut none = {};
-    if (phase == 0) {
-        DISPATCH(c, moments(c->dp, c->s, c->stream));
-    } else if (phase == 1) {
-        DISPATCH(c, ghosts(c->dp, c->s, c->stream));
-        if (c->s.nghost == 0) return TLB_OK;
-    } else if (phase == 2) {
-        DISPATCH(c, step(c->dp, c->s, MODE_STEP, nullptr, none, c->stream));
+    if (phase < 0 || phase > 2) return fail(TLB_E_INVAL, "phase must be 0, 1 or 2");
+    if (phase == 1 && c->s.nghost == 0) return TLB_OK;
+    issue_phase(c, phase, c->stream);
+    if (phase == 2) {
         c->s.cur ^= 1;
         c->steps += 1;
-    } else {
-        return fail(TLB_E_INVAL, "phase must be 0, 1 or 2");
     }
     return check_launch(c, 1);
 }
@@ -963,7 +1029,7 @@ static int build_plan(tlb_ctx *const *ctxs, int n, BatchPlan &plan, cudaStream_t
     for (int k = 0; k < n; ++k) {
         tlb_ctx *c = ctxs[k];
         if (c->D != D) return fail(TLB_E_INVAL, "batched lattices must share the lattice type");
-        if (c->p.g_fp16) return fail(TLB_E_UNSUPPORTED, "batched stepping supports FP32 g only");
+        if (c->p.g_fp16 != ctxs[0]->p.g_fp16) return fail(TLB_E_INVAL, "batched lattices must share the g storage");
         for (int par = 0; par < 2; ++par) {
             BatchEntry &e = par ? e1[k] : e0[k];
             int cur = (c->s.cur + par) & 1;
@@ -1007,14 +1073,15 @@ static int run_plan(BatchPlan &plan, int nsteps, cudaStream_t st)
     int D = plan.ctxs[0]->D;
     for (int s = 0; s < nsteps; ++s) {
         const BatchEntry *E = plan.entries[s & 1];
+        int fp16 = plan.ctxs[0]->p.g_fp16;
         if (D == 2) {
-            Launch<2>::moments_batch(E, plan.tiles, plan.ntiles, st);
+            Launch<2>::moments_batch(E, plan.tiles, plan.ntiles, fp16, st);
             ghosts_batch_launch<2>(E, plan.glist, plan.nglist, st);
-            Launch<2>::step_batch(E, plan.tiles, plan.ntiles, st);
+            Launch<2>::step_batch(E, plan.tiles, plan.ntiles, fp16, st);
         } else {
-            Launch<3>::moments_batch(E, plan.tiles, plan.ntiles, st);
+            Launch<3>::moments_batch(E, plan.tiles, plan.ntiles, fp16, st);
             ghosts_batch_launch<3>(E, plan.glist, plan.nglist, st);
-            Launch<3>::step_batch(E, plan.tiles, plan.ntiles, st);
+            Launch<3>::step_batch(E, plan.tiles, plan.ntiles, fp16, st);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -1168,15 +1235,9 @@ extern "C" int tlb_server_pump(tlb_server *s)
     // advance the active lattices together, grouped by lattice type and g storage
     int chunk = s->steps_per_round;
     for (Req *q : s->active) chunk = std::min(chunk, q->nsteps - q->done_steps);
-    std::vector<tlb_ctx *> groups[2];
-    for (Req *q : s->active) {
-        if (q->ctx->p.g_fp16) {
-            tlb_step(q->ctx, chunk);
-            continue;
-        }
-        groups[q->ctx->D == 3].push_back(q->ctx);
-    }
-    for (int g = 0; g < 2; ++g)
+    std::vector<tlb_ctx *> groups[4];      // by lattice type and g storage
+    for (Req *q : s->active) groups[(q->ctx->D == 3 ? 1 : 0) + (q->ctx->p.g_fp16 ? 2 : 0)].push_back(q->ctx);
+    for (int g = 0; g < 4; ++g)
         if (!groups[g].empty()) {
             int rc = tlb_step_batch(groups[g].data(), (int)groups[g].size(), chunk);
             if (rc) return rc;

@@ -84,8 +84,8 @@ struct Launch {
     static void convert_pop(const DevParams &p, const DevState &s, int dir, double *fbuf, double *gbuf,
                             cudaStream_t st);
     // batched: entries[0..n) and a tile table (tile -> entry, tile coords)
-    static void moments_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, cudaStream_t st);
-    static void step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, cudaStream_t st);
+    static void moments_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st);
+    static void step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st);
     static int tile_dims(int a);
 };
 

@@ -552,14 +552,21 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_kernel(DevParams p, 
     step_tile<D, GT, MODE>(p, f_in, f_out, g_in, g_out, rho, phi, type, status, x0, y0, z0, u_init, aux);
 }
 
+// The stepping kernel of every lattice, alone or batched: one CTA per entry of
+// a tile table (lattice index, tile origin).  A lattice advanced alone is a
+// batch of one, so its results are bit-identical to the same lattice in a mix.
 template <int D, typename GT>
 __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
 {
-    int4 t = tiles[blockIdx.x];
-    const BatchEntry &e = E[t.x];
+    __shared__ BatchEntry se;
+    const int4 t = tiles[blockIdx.x];
+    static_assert(sizeof(BatchEntry) % 4 == 0 && sizeof(BatchEntry) / 4 <= 256, "entry copy");
+    if (threadIdx.x < sizeof(BatchEntry) / 4)
+        reinterpret_cast<int *>(&se)[threadIdx.x] = reinterpret_cast<const int *>(&E[t.x])[threadIdx.x];
+    __syncthreads();
     AuxOut none = {};
-    step_tile<D, GT, MODE_STEP>(e.p, e.f_in, e.f_out, e.g_in, e.g_out, e.rho, e.phi, e.type, e.status, t.y, t.z, t.w,
-                                nullptr, none);
+    step_tile<D, GT, MODE_STEP>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type, se.status, t.y, t.z,
+                                t.w, nullptr, none);
 }
 
 // ---------------------------------------------------------------------------
@@ -743,16 +750,22 @@ void Launch<D>::convert_pop(const DevParams &p, const DevState &s, int dir, doub
 }
 
 template <int D>
-void Launch<D>::moments_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, cudaStream_t st)
+void Launch<D>::moments_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st)
 {
-    if (ntiles > 0)
+    if (ntiles <= 0) return;
+    if (g_fp16)
+        moments_batch_kernel<D, __half><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
+    else
         moments_batch_kernel<D, float><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
 }
 
 template <int D>
-void Launch<D>::step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, cudaStream_t st)
+void Launch<D>::step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st)
 {
-    if (ntiles > 0)
+    if (ntiles <= 0) return;
+    if (g_fp16)
+        step_batch_kernel<D, __half><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
+    else
         step_batch_kernel<D, float><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
 }
 
