@@ -216,6 +216,9 @@ def run_ours(args):
             "roofline": roofline(lb.Q, lb.N, bkms, peak, peak_kind,
                                  "step_kernel<D3Q27> (stencils, force, collision, stream)")}
         lb.close()
+    if rank == 0 and not args.no_batch:
+        result["batched"] = batched_sweep()
+        result["served"] = served_mix()
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
     if world > 1:
@@ -248,6 +251,97 @@ def e2e_run(wl, tlb, nsteps=1000, reps=3):
     return {"value": round(N * nsteps / t / 1e6, 2), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d / nsteps, 1),
             "d2h_bytes_per_step": round(d2h / nsteps, 1),
             "job": "tlb_init_fields (host FP64) + %d steps + tlb_get_fields (host FP64)" % nsteps}
+
+
+def batched_sweep(steps=10):
+    """The contact-angle sweep (512 D2Q9 lattices, 64^2-512^2, 43.8 M nodes):
+    all lattices advanced by tlb_step_batch (one launch per phase) against the
+    same lattices advanced one after another by tlb_step."""
+    import torch
+
+    from paper_1904_06881_gb300 import tlb
+    from paper_1904_06881_gb300 import workloads as W
+
+    items = W.c3_sweep()
+    lats = [tlb.lattice_from_workload(W.c3_lattice(it)) for it in items]
+    nodes = sum(l.N for l in lats)
+    handles = [l.h for l in lats]
+    tlb.tlb_step_batch(handles, 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tlb.tlb_step_batch(handles, steps)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    for l in lats:
+        l.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for l in lats:
+        l.step(steps)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    for l in lats:
+        l.sync()
+    res = {"workload": "c3 sweep: %d D2Q9 lattices, %d nodes" % (len(lats), nodes),
+           "batched_mlups": round(nodes * steps / tb / 1e6, 1), "sequential_mlups": round(nodes * steps / ts / 1e6, 1),
+           "speedup": round(ts / tb, 3), "steps": steps,
+           "l2": "state %.1f GB, larger than L2" % (sum(l.device_bytes for l in lats) / 1e9)}
+    for l in lats:
+        l.close()
+    return res
+
+
+def served_mix(budget_gb=24.0, max_active=64, steps_per_round=100):
+    """Poisson arrivals (20/s) of 64 requests (drops, channels, lubricated
+    substrates; see workloads.c4_requests) into the continuous-batching
+    server; p50/p99 time from submission to result and aggregate MLUPS over
+    the makespan, against the same requests run one after another alone."""
+    import torch
+
+    from paper_1904_06881_gb300 import tlb
+    from paper_1904_06881_gb300 import workloads as W
+
+    reqs = W.c4_requests()
+    work = sum(w["nx"] * w["ny"] * w["nz"] * n for _, w, n in reqs)
+    srv = tlb.Server(int(budget_gb * (1 << 30)), max_active=max_active, steps_per_round=steps_per_round)
+    t_start = time.perf_counter()
+    pending = list(range(len(reqs)))
+    tickets, lat = {}, {}
+    while len(lat) < len(reqs):
+        now = time.perf_counter() - t_start
+        while pending and reqs[pending[0]][0] <= now:
+            k = pending.pop(0)
+            _, wl, n = reqs[k]
+            tickets[k] = srv.submit(wl["lattice"], wl["nx"], wl["ny"], wl["nz"], wl["mask"], wl["rho"], wl["phi"], n,
+                                    **wl["params"])
+        srv.pump()
+        for k, t in list(tickets.items()):
+            if k in lat:
+                continue
+            r = srv.poll(t)
+            if r["state"] in (tlb.REQ_DONE, tlb.REQ_FAILED):
+                if r["state"] != tlb.REQ_DONE:
+                    raise RuntimeError("served request %d failed: %s" % (k, r["status"]))
+                lat[k] = r["done_s"] - r["submit_s"]
+        if not tickets and pending:
+            time.sleep(max(0.0, reqs[pending[0]][0] - (time.perf_counter() - t_start)))
+    makespan = time.perf_counter() - t_start
+    srv.close()
+    # the same requests one after another, each alone
+    t0 = time.perf_counter()
+    for _, wl, n in reqs:
+        l = tlb.lattice_from_workload(wl)
+        l.step(n)
+        l.sync()
+        l.close()
+    torch.cuda.synchronize()
+    tseq = time.perf_counter() - t0
+    lats = np.array([lat[k] for k in sorted(lat)])
+    return {"workload": "c4 served mix: %d requests, Poisson 20/s, %.2f G node-steps" % (len(reqs), work / 1e9),
+            "p50_s": round(float(np.percentile(lats, 50)), 4), "p99_s": round(float(np.percentile(lats, 99)), 4),
+            "aggregate_mlups": round(work / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
+            "arrival_span_s": round(reqs[-1][0], 3), "sequential_alone_mlups": round(work / tseq / 1e6, 1),
+            "server": {"budget_gb": budget_gb, "max_active": max_active, "steps_per_round": steps_per_round}}
 
 
 def cpu_baseline(wl, seconds=15.0):
@@ -321,6 +415,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the D3Q27 192x192x128 measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the served mix")
     ap.add_argument("--only", choices=["c1", "c2"], help="time one lattice only (profiling runs): no e2e, no CPU baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

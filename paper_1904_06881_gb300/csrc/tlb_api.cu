@@ -265,7 +265,37 @@ extern "C" int tlb_params_default(tlb_params *p)
     return TLB_OK;
 }
 
+static int derive_uncached(const tlb_params &p, tlb_derived &d);
+
+// The coexistence solve takes tens of milliseconds; contexts created with the
+// same EOS constants and densities (every request of a served mix) reuse it.
 static int derive(const tlb_params &p, tlb_derived &d)
+{
+    struct Key {
+        double a, b, R, rho_l, rho_g, k0, k1, k2, chi;
+        bool operator==(const Key &o) const { return std::memcmp(this, &o, sizeof(Key)) == 0; }
+    };
+    static std::mutex mu;
+    static std::vector<std::pair<Key, tlb_derived>> cache;
+    Key k = {p.a, p.b, p.R, p.rho_l, p.rho_g, p.kappa[0], p.kappa[1], p.kappa[2], p.chi};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &e : cache)
+            if (e.first == k) {
+                d = e.second;
+                return TLB_OK;
+            }
+    }
+    int rc = derive_uncached(p, d);
+    if (rc == TLB_OK) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (cache.size() >= 16) cache.erase(cache.begin());
+        cache.push_back({k, d});
+    }
+    return rc;
+}
+
+static int derive_uncached(const tlb_params &p, tlb_derived &d)
 {
     if (!(p.rho_l > p.rho_g && p.rho_g > 0)) return fail(TLB_E_INVAL, "need rho_l > rho_g > 0");
     if (!(p.a > 0 && p.b > 0 && p.R > 0)) return fail(TLB_E_INVAL, "EOS constants must be positive");

@@ -152,10 +152,23 @@ def c3_sweep(seed=3, n=256, sizes=(64, 128, 256, 512)):
     return out
 
 
+def provisional_kw(theta_deg):
+    """Force-method strength for a target angle from a linear fit of sessile
+    drops run with the FP64 oracle (radius 16, 64x64: kappa^w = +0.2 gives
+    76 deg, -0.2 gives 102 deg), clipped to |kappa^w| <= 0.3.  Not a
+    calibration: used only to give every force-wetting lattice of a sweep a
+    strength of the right sign and size."""
+    return float(np.clip((90.0 - theta_deg) / 65.0, -0.3, 0.3))
+
+
 def c3_lattice(item):
     L = item["L"]
     mask, rho, phi = sessile_drop_2d(L, L, L / 4.0, xc=L / 2.0, yc=0.5)
     th = (item["theta"], item["theta"], 90.0)
+    if item["wetting"] == WET_FORCE:
+        params = base_params(wetting=WET_FORCE, kw_rho=provisional_kw(item["theta"]))
+        return dict(name="c3_drop_%d" % L, lattice=D2Q9, nx=L, ny=L, nz=1, params=params,
+                    mask=mask, rho=rho, phi=phi, steps=5000)
     params = base_params(wetting=item["wetting"], theta_deg=th)
     return dict(name="c3_drop_%d" % L, lattice=D2Q9, nx=L, ny=L, nz=1, params=params,
                 mask=mask, rho=rho, phi=phi, steps=5000)
@@ -169,3 +182,32 @@ def big_periodic_drop_2d(n=4096, R=None):
     rho, phi = phase_fields(C2, np.zeros_like(C2))
     return dict(name="big_d2q9_%d" % n, lattice=D2Q9, nx=n, ny=n, nz=1, params=base_params(),
                 mask=np.zeros((1, n, n), np.uint8), rho=rho[None], phi=phi[None], steps=1000)
+
+
+def c4_requests(seed=4, n=64, rate=20.0):
+    """Served mix: Poisson arrivals (mean `rate` per second) of requests drawn
+    from sessile drops (64^2-256^2), capillary channels (256x64-1024x64) and
+    lubricated substrates (D3Q27 48^3-96^3), with uniform random angles in
+    [30, 150] deg (geometric interpolation) and 1000-3000 steps (2D) or
+    300-800 steps (3D).  Returns a list of (arrival_s, workload dict, steps)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    out = []
+    for k in range(n):
+        kind = rng.choice(["drop", "channel", "lubricated"], p=[0.5, 0.35, 0.15])
+        th = float(rng.uniform(30.0, 150.0))
+        if kind == "drop":
+            L = int(rng.choice([64, 128, 256]))
+            wl = c3_lattice(dict(L=L, theta=th, wetting=WET_GEOM_INTERP))
+            steps = int(rng.integers(1000, 3001))
+        elif kind == "channel":
+            nx = int(rng.choice([256, 512, 1024]))
+            wl = c1_capillary(nx=nx, ny=64, x_in=nx // 4, x_out=nx - nx // 16)
+            wl["params"] = base_params(wetting=WET_GEOM_INTERP, theta_deg=(th, 60.0, 120.0))
+            steps = int(rng.integers(1000, 3001))
+        else:
+            n3 = int(rng.choice([48, 64, 96]))
+            wl = c2_lubricated(nx=n3, ny=n3, nz=n3, R=n3 / 6.0, lub=3, gap=2, kw_rho=0.02)
+            steps = int(rng.integers(300, 801))
+        out.append((float(t[k]), wl, steps))
+    return out
