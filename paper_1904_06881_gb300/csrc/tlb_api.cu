@@ -20,11 +20,6 @@
 #include "tlb_device.cuh"
 #include "tlb_internal.h"
 
-namespace tlb {
-template <int D>
-void ghosts_batch_launch(const BatchEntry *entries, const int2 *gl, int n, cudaStream_t st);
-}
-
 using namespace tlb;
 
 // ---------------------------------------------------------------------------
@@ -392,12 +387,10 @@ struct tlb_ctx {
     long long steps = 0;
     long long launches = 0;
     int sticky = TLB_OK;
-    // the lattice as a batch of one: entries for both buffer parities, tile table, ghost list
+    // the lattice as a batch of one: entries for both buffer parities, tile table
     BatchEntry *self_entries = nullptr;
     int4 *self_tiles = nullptr;
     int nself_tiles = 0;
-    int2 *self_glist = nullptr;
-    size_t self_glist_cap = 0;
     // one CUDA graph per buffer parity holding the three launches of a step
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaStream_t cap_stream = nullptr;
@@ -674,19 +667,6 @@ extern "C" int tlb_set_solid(tlb_ctx *c, const uint8_t *mask)
     if (ng) CUDA_TRY(cudaMemcpyAsync(c->ghosts_dev, c->ghost_host.data(), ng * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     c->s.ghosts = c->ghosts_dev;
     c->s.nghost = (int)ng;
-    if (ng > c->self_glist_cap) {
-        void *ptr;
-        int rc = dev_alloc(c->owned, &ptr, ng * sizeof(int2), &c->bytes);
-        if (rc) return rc;
-        c->self_glist = (int2 *)ptr;
-        c->self_glist_cap = ng;
-    }
-    if (ng) {
-        std::vector<int2> gl(ng);
-        for (size_t k = 0; k < ng; ++k) gl[k] = make_int2(0, c->ghost_host[k]);
-        CUDA_TRY(cudaMemcpyAsync(c->self_glist, gl.data(), ng * sizeof(int2), cudaMemcpyHostToDevice, c->stream));
-        CUDA_TRY(cudaStreamSynchronize(c->stream));
-    }
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return TLB_OK;
 }
@@ -771,19 +751,16 @@ static void issue_phase(tlb_ctx *c, int phase, cudaStream_t st)
     int fp16 = c->p.g_fp16;
     if (c->D == 2) {
         if (phase == 0) Launch<2>::moments_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
-        else if (phase == 1) ghosts_batch_launch<2>(E, c->self_glist, c->s.nghost, st);
-        else Launch<2>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
+        else if (phase == 2) Launch<2>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
     } else {
         if (phase == 0) Launch<3>::moments_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
-        else if (phase == 1) ghosts_batch_launch<3>(E, c->self_glist, c->s.nghost, st);
-        else Launch<3>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
+        else if (phase == 2) Launch<3>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
     }
 }
 
 static void issue_step_on(tlb_ctx *c, cudaStream_t st)
 {
     issue_phase(c, 0, st);
-    issue_phase(c, 1, st);
     issue_phase(c, 2, st);
 }
 
@@ -811,7 +788,7 @@ extern "C" int tlb_step(tlb_ctx *c, int nsteps)
 {
     if (!c) return fail(TLB_E_INVAL, "null context");
     if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
-    int per = (c->s.nghost > 0) ? 3 : 2;
+    const int per = 2;
     for (int k = 0; k < nsteps; ++k) {
         int rc = capture_step(c);
         if (rc) return rc;
@@ -829,7 +806,7 @@ extern "C" int tlb_step_phase(tlb_ctx *c, int phase)
 {
     if (!c) return fail(TLB_E_INVAL, "null context");
     if (phase < 0 || phase > 2) return fail(TLB_E_INVAL, "phase must be 0, 1 or 2");
-    if (phase == 1 && c->s.nghost == 0) return TLB_OK;
+    if (phase == 1) return TLB_OK;        // the ghost layer is filled inside phase 2
     issue_phase(c, phase, c->stream);
     if (phase == 2) {
         c->s.cur ^= 1;
@@ -1043,15 +1020,13 @@ struct BatchPlan {
     std::vector<Block> owned;
     BatchEntry *entries[2] = {nullptr, nullptr};   // parity of the step
     int4 *tiles = nullptr;
-    int2 *glist = nullptr;
-    int ntiles = 0, nglist = 0;
+    int ntiles = 0;
 };
 
 static int build_plan(tlb_ctx *const *ctxs, int n, BatchPlan &plan, cudaStream_t st)
 {
     int D = ctxs[0]->D;
     std::vector<int4> tiles;
-    std::vector<int2> gl;
     std::vector<BatchEntry> e0(n), e1(n);
     int TX = D == 2 ? Launch<2>::tile_dims(0) : Launch<3>::tile_dims(0);
     int TY = D == 2 ? Launch<2>::tile_dims(1) : Launch<3>::tile_dims(1);
@@ -1076,7 +1051,6 @@ static int build_plan(tlb_ctx *const *ctxs, int n, BatchPlan &plan, cudaStream_t
         for (int z = 0; z < c->p.nz; z += TZ)
             for (int y = 0; y < c->p.ny; y += TY)
                 for (int x = 0; x < c->p.nx; x += TX) tiles.push_back(make_int4(k, x, y, z));
-        for (int g : c->ghost_host) gl.push_back(make_int2(k, g));
     }
     void *ptr;
     int rc;
@@ -1086,14 +1060,10 @@ static int build_plan(tlb_ctx *const *ctxs, int n, BatchPlan &plan, cudaStream_t
     plan.entries[1] = (BatchEntry *)ptr;
     if ((rc = dev_alloc(plan.owned, &ptr, tiles.size() * sizeof(int4), nullptr))) return rc;
     plan.tiles = (int4 *)ptr;
-    if ((rc = dev_alloc(plan.owned, &ptr, std::max<size_t>(gl.size(), 1) * sizeof(int2), nullptr))) return rc;
-    plan.glist = (int2 *)ptr;
     CUDA_TRY(cudaMemcpyAsync(plan.entries[0], e0.data(), n * sizeof(BatchEntry), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(plan.entries[1], e1.data(), n * sizeof(BatchEntry), cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(plan.tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-    if (!gl.empty()) CUDA_TRY(cudaMemcpyAsync(plan.glist, gl.data(), gl.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
     plan.ntiles = (int)tiles.size();
-    plan.nglist = (int)gl.size();
     plan.ctxs.assign(ctxs, ctxs + n);
     return TLB_OK;
 }
@@ -1106,17 +1076,15 @@ static int run_plan(BatchPlan &plan, int nsteps, cudaStream_t st)
         int fp16 = plan.ctxs[0]->p.g_fp16;
         if (D == 2) {
             Launch<2>::moments_batch(E, plan.tiles, plan.ntiles, fp16, st);
-            ghosts_batch_launch<2>(E, plan.glist, plan.nglist, st);
             Launch<2>::step_batch(E, plan.tiles, plan.ntiles, fp16, st);
         } else {
             Launch<3>::moments_batch(E, plan.tiles, plan.ntiles, fp16, st);
-            ghosts_batch_launch<3>(E, plan.glist, plan.nglist, st);
             Launch<3>::step_batch(E, plan.tiles, plan.ntiles, fp16, st);
         }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(TLB_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
-    int per = plan.nglist > 0 ? 3 : 2;
+    const int per = 2;
     for (tlb_ctx *c : plan.ctxs) {
         if (nsteps & 1) c->s.cur ^= 1;
         c->steps += nsteps;

@@ -8,13 +8,15 @@
 //   rho, phi : float[N] moments of the current state; solid ghost nodes hold
 //              the ghost-layer values of Sec. IV
 //   type : uint8[N]  node flags (TLB_SOLID, TLB_FIRST, TLB_GHOST, wall axes)
-// One step = three launches:
-//   moments_kernel  : rho = 1 + sum_i f~_i, phi = sum_i g_i       (reads 2Q floats)
-//   ghost_kernel    : ghost-layer rho, phi over the ghost-node list  (small)
-//   step_kernel     : tile + halo of rho, phi in shared memory -> stencils,
-//                     chemical potentials, pressure tensor (halo 1) -> force
-//                     with wall rules -> ELBM collision of f (entropic alpha),
-//                     LBGK of g -> push streaming with halfway bounce-back.
+// One step = two launches (the same kernels for one lattice and for a batch,
+// through a tile -> lattice table):
+//   moments_batch_kernel : rho = 1 + sum_i f~_i, phi = sum_i g_i  (reads 2Q values)
+//   step_batch_kernel    : tile + halo 2 of rho, phi in shared memory, ghost
+//                          layer filled there from the fluid moments -> stencils,
+//                          chemical potentials, pressure tensor (halo 1) -> force
+//                          with wall rules -> ELBM collision of f (entropic
+//                          alpha), LBGK of g -> push streaming with halfway
+//                          bounce-back.
 #pragma once
 #include <cuda_fp16.h>
 #include <stdint.h>

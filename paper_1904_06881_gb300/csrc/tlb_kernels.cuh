@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(256) moments_batch_kernel(const BatchEntry *__
 // with only diagonal fluid neighbours take the mean of those neighbours.
 // ---------------------------------------------------------------------------
 template <int D>
-__device__ void ghost_node(const DevParams &p, const uint8_t *__restrict__ type, float *rho, float *phi, long long n)
+__device__ void ghost_value(const DevParams &p, const uint8_t *__restrict__ type, const float *rho, const float *phi,
+                            long long n, float &gr_out, float &gp_out)
 {
     constexpr int Q = Lat<D>::Q;
     int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
@@ -116,10 +117,17 @@ __device__ void ghost_node(const DevParams &p, const uint8_t *__restrict__ type,
             ++cnt;
         }
     }
-    if (cnt > 0) {
-        rho[n] = sr / (float)cnt;
-        phi[n] = sp / (float)cnt;
-    }
+    gr_out = cnt > 0 ? sr / (float)cnt : 0.f;
+    gp_out = cnt > 0 ? sp / (float)cnt : 0.f;
+}
+
+template <int D>
+__device__ void ghost_node(const DevParams &p, const uint8_t *__restrict__ type, float *rho, float *phi, long long n)
+{
+    float gr, gp;
+    ghost_value<D>(p, type, rho, phi, n, gr, gp);
+    rho[n] = gr;
+    phi[n] = gp;
 }
 
 template <int D>
@@ -129,17 +137,6 @@ __global__ void __launch_bounds__(128) ghost_kernel(DevParams p, const uint8_t *
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nghost) return;
     ghost_node<D>(p, type, rho, phi, ghosts[k]);
-}
-
-// batched ghost list: (entry, node)
-template <int D>
-__global__ void __launch_bounds__(128) ghost_batch_kernel(const BatchEntry *__restrict__ E, const int2 *__restrict__ gl, int n)
-{
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int2 q = gl[k];
-    const BatchEntry &e = E[q.x];
-    ghost_node<D>(e.p, e.type, const_cast<float *>(e.rho), const_cast<float *>(e.phi), q.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -243,12 +240,21 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     __shared__ uint8_t stype[NS];
     const int tid = threadIdx.x;
 
-    // Stage A: rho, phi of the tile + halo 2; node flags of the tile + halo 1
+    // Stage A: rho, phi of the tile + halo 2, the ghost layer of Sec. IV filled
+    // here from the fluid moments (the moments pass leaves ghost nodes alone);
+    // node flags of the tile + halo 1
     for (int k = tid; k < NR; k += blockDim.x) {
         int lx = k % RX, ly = (k / RX) % RY, lz = k / (RX * RY);
         long long n = node_of(p, x0 - 2 + lx, y0 - 2 + ly, z0 - HZ2 + lz);
-        srho[k] = __ldg(rho + n);
-        sphi[k] = __ldg(phi + n);
+        if (__ldg(type + n) & TLB_GHOST) {
+            float gr, gp;
+            ghost_value<D>(p, type, rho, phi, n, gr, gp);
+            srho[k] = gr;
+            sphi[k] = gp;
+        } else {
+            srho[k] = __ldg(rho + n);
+            sphi[k] = __ldg(phi + n);
+        }
     }
     for (int k = tid; k < NS; k += blockDim.x) {
         int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
@@ -769,10 +775,5 @@ void Launch<D>::step_batch(const BatchEntry *entries, const int4 *tiles, int nti
         step_batch_kernel<D, float><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
 }
 
-template <int D>
-void ghosts_batch_launch(const BatchEntry *entries, const int2 *gl, int n, cudaStream_t st)
-{
-    if (n > 0) ghost_batch_kernel<D><<<(n + 127) / 128, 128, 0, st>>>(entries, gl, n);
-}
 
 }  // namespace tlb
