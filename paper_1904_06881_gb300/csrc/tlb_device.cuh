@@ -165,8 +165,8 @@ __device__ __forceinline__ float phi_ent(float y)
 //   e1 = a3 / (3 a2),  e2 = 2 (2 a3^2 - 3 a2 a4) / (9 a2^2),
 //   e3 = (297 a2^2 a5 - 420 a2 a3 a4 + 170 a3^3) / (270 a2^3),
 // used as is up to max|x| = 0.03 (its effect on f stays below 1e-8 there) and as
-// the start of Newton's method, bracketed by [1, alpha_max), above it; there
-// the Newton sums and ratio are FP64 (nodes at the interface).
+// the start of Newton's method, bracketed by [1, alpha_max), above it (nodes
+// at the interface); there the ratio h/h' of each Newton step is taken in FP64.
 template <int Q>
 __device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&x)[Q])
 {
@@ -188,32 +188,32 @@ __device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float 
     return 2.0f + e1 + e2 + e3;
 }
 
-template <int Q, typename Acc>
+template <int Q>
 __device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float (&x)[Q], float amax, float al)
 {
     float L[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) L[i] = log1pf(x[i]);
-    auto hval = [&](float a, Acc &dh) {
-        Acc h = 0;
-        dh = 0;
+    auto hval = [&](float a, float &dh) {
+        float h = 0.f;
+        dh = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float y = a * x[i];
-            h += (Acc)(fp[i] * (phi_ent(y) - y * L[i]));
-            dh += (Acc)(fp[i] * x[i] * (log1pf(y) - L[i]));
+            h += fp[i] * (phi_ent(y) - y * L[i]);
+            dh += fp[i] * x[i] * (log1pf(y) - L[i]);
         }
         return h;
     };
     float lo = 1.0f, hi = amax * (1.0f - 1e-6f);
-    Acc dh;
-    if (hi < 4.0f && hval(hi, dh) < (Acc)0) return hi;      // no root below the positivity bound
+    float dh;
+    if (hi < 4.0f && hval(hi, dh) < 0.f) return hi;      // no root below the positivity bound
     if (!(al > lo && al < hi)) al = 0.5f * (lo + hi);
     for (int it = 0; it < 16; ++it) {
-        Acc h = hval(al, dh);
-        if (h > (Acc)0) hi = al; else lo = al;
-        if (dh > (Acc)0) {
-            float step = (float)(h / dh);
+        float h = hval(al, dh);
+        if (h > 0.f) hi = al; else lo = al;
+        if (dh > 0.f) {
+            float step = (float)((double)h / (double)dh);
             if (fabsf(step) <= 1e-6f * al) {   // converged: accept the last Newton step
                 al -= step;
                 break;

@@ -36,8 +36,16 @@ struct Tile<2> {
 };
 template <>
 struct Tile<3> {
-    static constexpr int X = 16, Y = 8, Z = 2;
+    static constexpr int X = 8, Y = 8, Z = 4;
 };
+
+// periodic wrap of a coordinate at most one period outside [0, n)
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ long long node_near(const DevParams &p, int x, int y, int z)
+{
+    return (long long)wrap1(x, p.nx) + (long long)p.nx * ((long long)wrap1(y, p.ny) + (long long)p.ny * wrap1(z, p.nz));
+}
 
 // ---------------------------------------------------------------------------
 // moments: rho = 1 + sum_i (f_i - w_i), phi = sum_i g_i at fluid nodes
@@ -245,7 +253,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     // node flags of the tile + halo 1
     for (int k = tid; k < NR; k += blockDim.x) {
         int lx = k % RX, ly = (k / RX) % RY, lz = k / (RX * RY);
-        long long n = node_of(p, x0 - 2 + lx, y0 - 2 + ly, z0 - HZ2 + lz);
+        long long n = node_near(p, x0 - 2 + lx, y0 - 2 + ly, z0 - HZ2 + lz);
         if (__ldg(type + n) & TLB_GHOST) {
             float gr, gp;
             ghost_value<D>(p, type, rho, phi, n, gr, gp);
@@ -258,7 +266,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
     for (int k = tid; k < NS; k += blockDim.x) {
         int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
-        stype[k] = __ldg(type + node_of(p, x0 - 1 + lx, y0 - 1 + ly, z0 - HZ1 + lz));
+        stype[k] = __ldg(type + node_near(p, x0 - 1 + lx, y0 - 1 + ly, z0 - HZ1 + lz));
     }
     __syncthreads();
 
@@ -505,7 +513,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         al = alpha_series<Q>(fp, dl);
         if (xmax > 0.03f) {
             const float amax = xneg > 0.f ? 1.0f / xneg : 3.0e38f;
-            al = alpha_newton<Q, double>(fp, dl, amax, al);
+            al = alpha_newton<Q>(fp, dl, amax, al);
         }
     }
     const float ab = al * p.beta;
