@@ -47,6 +47,23 @@ __device__ __forceinline__ long long node_near(const DevParams &p, int x, int y,
     return (long long)wrap1(x, p.nx) + (long long)p.nx * ((long long)wrap1(y, p.ny) + (long long)p.ny * wrap1(z, p.nz));
 }
 
+// Asynchronous global -> shared copies (sm_80+ cp.async): the node's own
+// populations are requested before the tile stages and consumed after them.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// dynamic shared memory of the stepping kernel: f (and FP32 g) of the tile's own nodes
+template <int D, typename GT>
+__host__ __device__ constexpr int stage_bytes()
+{
+    return Lat<D>::Q * Tile<D>::X * Tile<D>::Y * Tile<D>::Z * 4 * (sizeof(GT) == 4 ? 2 : 1);
+}
+
 // ---------------------------------------------------------------------------
 // moments: rho = 1 + sum_i (f_i - w_i), phi = sum_i g_i at fluid nodes
 // ---------------------------------------------------------------------------
@@ -228,7 +245,7 @@ __device__ __forceinline__ int qcomp(int a, int b)
 // ---------------------------------------------------------------------------
 // The fused step kernel.  One CTA = one tile of TX x TY x TZ nodes.
 // ---------------------------------------------------------------------------
-template <int D, typename GT, int MODE>
+template <int D, typename GT, int MODE, bool ASYNC = false>
 __device__ __forceinline__ void step_tile(const DevParams &p, const float *__restrict__ f_in, float *__restrict__ f_out,
                                           const void *g_in, void *g_out, const float *__restrict__ rho,
                                           const float *__restrict__ phi, const uint8_t *__restrict__ type,
@@ -247,6 +264,22 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     __shared__ float smu[NS];
     __shared__ uint8_t stype[NS];
     const int tid = threadIdx.x;
+    constexpr int NT = TX * TY * TZ;
+    extern __shared__ float stage[];          // ASYNC: f[Q][NT], then FP32 g[Q][NT]
+    if (ASYNC) {
+        const int ax = x0 + tid % TX, ay = y0 + (tid / TX) % TY, az = z0 + tid / (TX * TY);
+        if (ax < p.nx && ay < p.ny && az < p.nz) {
+            const long long an = (long long)ax + (long long)p.nx * ((long long)ay + (long long)p.ny * az);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) cp_async4(&stage[i * NT + tid], f_in + (long long)i * p.N + an);
+            if (sizeof(GT) == 4) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    cp_async4(&stage[(Q + i) * NT + tid], (const float *)g_in + (long long)i * p.N + an);
+            }
+        }
+        cp_async_commit();
+    }
 
     // Stage A: rho, phi of the tile + halo 2, the ghost layer of Sec. IV filled
     // here from the fluid moments (the moments pass leaves ghost nodes alone);
@@ -296,6 +329,9 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         smu[k] = t.mup;
     }
     __syncthreads();
+
+    // every thread waits for its own staged copies before any thread can leave
+    if (ASYNC) cp_async_wait_all();
 
     // Stage C: one node per thread
     const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
@@ -440,7 +476,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float fi = __ldg(f_in + (long long)i * p.N + n);
+        float fi = ASYNC ? stage[i * NT + tid] : __ldg(f_in + (long long)i * p.N + n);
         fp[i] = fi;
 #pragma unroll
         for (int a = 0; a < D; ++a)
@@ -536,7 +572,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     float gsum = 0.f, g0 = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float gi = GIO<GT>::ld(g_in, (long long)i * p.N + n, p.g_unscale);
+        float gi = (ASYNC && sizeof(GT) == 4) ? stage[(Q + i) * NT + tid]
+                                               : GIO<GT>::ld(g_in, (long long)i * p.N + n, p.g_unscale);
         if (i == 0) { g0 = gi; continue; }
         float cv = 0.f;
 #pragma unroll
@@ -579,8 +616,8 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_batch_kernel(const B
         reinterpret_cast<int *>(&se)[threadIdx.x] = reinterpret_cast<const int *>(&E[t.x])[threadIdx.x];
     __syncthreads();
     AuxOut none = {};
-    step_tile<D, GT, MODE_STEP>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type, se.status, t.y, t.z,
-                                t.w, nullptr, none);
+    step_tile<D, GT, MODE_STEP, true>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type, se.status,
+                                      t.y, t.z, t.w, nullptr, none);
 }
 
 // ---------------------------------------------------------------------------
@@ -773,14 +810,24 @@ void Launch<D>::moments_batch(const BatchEntry *entries, const int4 *tiles, int 
         moments_batch_kernel<D, float><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
 }
 
+template <int D, typename GT>
+static void launch_step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, cudaStream_t st)
+{
+    constexpr int bytes = stage_bytes<D, GT>();
+    static bool attr = false;   // the dynamic shared-memory opt-in, once per process
+    if (!attr) {
+        cudaFuncSetAttribute(step_batch_kernel<D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        attr = true;
+    }
+    step_batch_kernel<D, GT><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, bytes, st>>>(entries, tiles);
+}
+
 template <int D>
 void Launch<D>::step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st)
 {
     if (ntiles <= 0) return;
-    if (g_fp16)
-        step_batch_kernel<D, __half><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
-    else
-        step_batch_kernel<D, float><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
+    if (g_fp16) launch_step_batch<D, __half>(entries, tiles, ntiles, st);
+    else launch_step_batch<D, float>(entries, tiles, ntiles, st);
 }
 
 
