@@ -30,6 +30,33 @@ FALLBACK_HBM = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 
 
+def kernel_source_hash():
+    """sha256 over the kernel sources (csrc/*.cu, *.cuh, *.h), in name order."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1904_06881_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload_name):
+    """DRAM bytes per launch of the step kernel from the committed ncu capture,
+    or None when the kernel sources changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    if t.get("source_sha256") != kernel_source_hash():
+        return None
+    return t.get("traffic_bytes_per_launch", {}).get(workload_name)
+
+
 def hbm_peak():
     try:
         with open(PEAKS_FILE) as fh:
@@ -149,11 +176,12 @@ def measure(lat, stream, steps, warmup, flush=None, kernel_steps=None):
     return step_ms, kern_ms, launches, wall
 
 
-def roofline(Q, N, kern_ms, peak, peak_kind, kernel_name):
+def roofline(Q, N, kern_ms, peak, peak_kind, kernel_name, workload_name):
     achieved = algorithmic_bytes(Q, N) / (kern_ms * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": peak_kind + " hbm_gbs of MEASURED_PEAKS.json",
-            "traffic": None, "kernel_ms": round(kern_ms, 5), "algorithmic_bytes_per_launch": algorithmic_bytes(Q, N)}
+            "traffic": measured_traffic(workload_name), "kernel_ms": round(kern_ms, 5),
+            "algorithmic_bytes_per_launch": algorithmic_bytes(Q, N)}
 
 
 def run_ours(args):
@@ -193,7 +221,8 @@ def run_ours(args):
                    "wetting": "geometric interpolation", "angles_deg": [30, 60, 120],
                    "density_ratio": 14.14, "l2": "256 MB buffer written before every timed step; steps timed alone",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline(Q, N, kern_ms, peak, peak_kind, "step_kernel<D2Q9> (stencils, force, collision, stream)"),
+        "roofline": roofline(Q, N, kern_ms, peak, peak_kind,
+                             "step_batch_kernel<D2Q9> (ghost layer, stencils, force, collision, stream)", wl["name"]),
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "host_wall_s": round(wall, 4),
@@ -214,7 +243,8 @@ def run_ours(args):
             "ms_per_step": round(bms, 4), "gpu_launches": int(blaunch), "clocks": clk2.summary(),
             "l2": "state 2.1 GB, larger than L2; no flush",
             "roofline": roofline(lb.Q, lb.N, bkms, peak, peak_kind,
-                                 "step_kernel<D3Q27> (stencils, force, collision, stream)")}
+                                 "step_batch_kernel<D3Q27> (ghost layer, stencils, force, collision, stream)",
+                                 big["name"])}
         lb.close()
     if rank == 0 and not args.no_batch:
         result["batched"] = batched_sweep()
