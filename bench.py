@@ -110,6 +110,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(value, device=None):
+    """The largest value over the ranks of the default process group (the
+    job's time is the slowest replica's); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -208,9 +221,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         step_ms, kern_ms, launches, wall = measure(lat, stream, args.steps, args.warmup, flush=flush)
     if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+        step_ms = max_over_ranks(step_ms, device="cuda")
     value = world * N / (step_ms * 1e-3) / 1e6
     peak, peak_kind = hbm_peak()
     result = {
