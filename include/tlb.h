@@ -60,7 +60,8 @@ typedef struct {
     int    wetting;              /* TLB_WET_* (Sec. IV.A-B) */
     double theta_deg[3];         /* theta_21, theta_31, theta_23 (Sec. IV.A convention) */
     double kw_rho, kw_phi;       /* force-method strengths (Eq. forceBC) */
-    int    g_fp16;               /* 1: store g as FP16 scaled by 1/chi (reduced precision) */
+    int    g_fp16;               /* 1: reduced-precision g storage: the rest population g_0 in
+                                    FP32, the moving populations in FP16 scaled by 16 */
 } tlb_params;
 
 /* Constants derived at creation (host FP64). */

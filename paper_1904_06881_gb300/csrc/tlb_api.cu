@@ -360,8 +360,8 @@ static DevParams make_dev(const tlb_params &p, const tlb_derived &d)
     q.kw_rho = (float)p.kw_rho;
     q.kw_phi = (float)p.kw_phi;
     q.g_fp16 = p.g_fp16;
-    q.g_scale = p.g_fp16 ? (float)(1.0 / p.chi) : 1.0f;
-    q.g_unscale = p.g_fp16 ? (float)p.chi : 1.0f;
+    q.g_scale = p.g_fp16 ? 16.0f : 1.0f;        // moving g populations are O(0.1) or smaller
+    q.g_unscale = p.g_fp16 ? 1.0f / 16.0f : 1.0f;
     return q;
 }
 
@@ -406,6 +406,14 @@ static void drop_graphs(tlb_ctx *c)
 }
 
 static int Qof(int lattice) { return lattice == TLB_D3Q27 ? 27 : 9; }
+
+// bytes of one copy of the g populations: FP32 [Q][N], or g_0 in FP32 plus the
+// moving populations in FP16
+static size_t g_bytes(int lattice, size_t N, int fp16)
+{
+    size_t Q = (size_t)Qof(lattice);
+    return fp16 ? N * 4 + (Q - 1) * N * 2 : Q * N * 4;
+}
 static int Dof(int lattice) { return lattice == TLB_D3Q27 ? 3 : 2; }
 
 #define DISPATCH(ctx, call)                       \
@@ -465,7 +473,7 @@ extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
     c->Q = Qof(c->p.lattice);
     c->N = c->dp.N;
     size_t N = (size_t)c->N, Q = (size_t)c->Q;
-    size_t gsz = c->p.g_fp16 ? 2 : 4;
+    size_t gb = g_bytes(c->p.lattice, N, c->p.g_fp16);
     void *ptr;
 #define ALLOC(field, nbytes)                                             \
     do {                                                                 \
@@ -475,8 +483,8 @@ extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
     } while (0)
     ALLOC(c->s.f[0], Q * N * 4);
     ALLOC(c->s.f[1], Q * N * 4);
-    ALLOC(c->s.g[0], Q * N * gsz);
-    ALLOC(c->s.g[1], Q * N * gsz);
+    ALLOC(c->s.g[0], gb);
+    ALLOC(c->s.g[1], gb);
     ALLOC(c->s.rho, N * 4);
     ALLOC(c->s.phi, N * 4);
     ALLOC(c->s.type, N);
@@ -491,9 +499,9 @@ extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
     cudaMemsetAsync(c->s.type, 0, N, c->stream);
     cudaMemsetAsync(c->s.status, 0, 256, c->stream);
     cudaMemsetAsync(c->s.f[0], 0, Q * N * 4, c->stream);
-    cudaMemsetAsync(c->s.g[0], 0, Q * N * gsz, c->stream);
+    cudaMemsetAsync(c->s.g[0], 0, gb, c->stream);
     cudaMemsetAsync(c->s.f[1], 0, Q * N * 4, c->stream);
-    cudaMemsetAsync(c->s.g[1], 0, Q * N * gsz, c->stream);
+    cudaMemsetAsync(c->s.g[1], 0, gb, c->stream);
     cudaMemsetAsync(c->s.rho, 0, N * 4, c->stream);
     cudaMemsetAsync(c->s.phi, 0, N * 4, c->stream);
     c->type_host.assign(N, 0);
@@ -974,14 +982,14 @@ extern "C" size_t tlb_snapshot_bytes(const tlb_ctx *c)
 {
     if (!c) return 0;
     size_t QN = (size_t)c->Q * (size_t)c->N;
-    return sizeof(SnapHeader) + QN * 4 + QN * (c->p.g_fp16 ? 2 : 4);
+    return sizeof(SnapHeader) + QN * 4 + g_bytes(c->p.lattice, (size_t)c->N, c->p.g_fp16);
 }
 
 extern "C" int tlb_snapshot(tlb_ctx *c, void *host, size_t bytes)
 {
     if (!c || !host) return fail(TLB_E_INVAL, "null argument");
     if (bytes < tlb_snapshot_bytes(c)) return fail(TLB_E_INVAL, "snapshot buffer too small");
-    size_t QN = (size_t)c->Q * (size_t)c->N, gb = QN * (c->p.g_fp16 ? 2 : 4);
+    size_t QN = (size_t)c->Q * (size_t)c->N, gb = g_bytes(c->p.lattice, (size_t)c->N, c->p.g_fp16);
     SnapHeader h = {0x544c4253u, (uint64_t)c->N, (uint64_t)c->Q, (uint64_t)gb, c->steps};
     std::memcpy(host, &h, sizeof(h));
     char *dst = (char *)host + sizeof(h);
@@ -997,7 +1005,7 @@ extern "C" int tlb_restore(tlb_ctx *c, const void *host, size_t bytes)
     if (bytes < tlb_snapshot_bytes(c)) return fail(TLB_E_INVAL, "snapshot buffer too small");
     SnapHeader h;
     std::memcpy(&h, host, sizeof(h));
-    size_t QN = (size_t)c->Q * (size_t)c->N, gb = QN * (c->p.g_fp16 ? 2 : 4);
+    size_t QN = (size_t)c->Q * (size_t)c->N, gb = g_bytes(c->p.lattice, (size_t)c->N, c->p.g_fp16);
     if (h.magic != 0x544c4253u || h.N != (uint64_t)c->N || h.Q != (uint64_t)c->Q || h.gbytes != gb)
         return fail(TLB_E_INVAL, "snapshot does not match this context");
     const char *src = (const char *)host + sizeof(h);
@@ -1145,7 +1153,7 @@ struct tlb_server {
 static size_t footprint(const tlb_params &p)
 {
     size_t N = (size_t)p.nx * p.ny * p.nz, Q = (size_t)Qof(p.lattice);
-    return 2 * Q * N * 4 + 2 * Q * N * (p.g_fp16 ? 2 : 4) + N * 9 + (1 << 16);
+    return 2 * Q * N * 4 + 2 * g_bytes(p.lattice, N, p.g_fp16) + N * 9 + (1 << 16);
 }
 
 extern "C" int tlb_server_create(size_t budget, int max_active, int steps_per_round, void *stream, tlb_server **out)

@@ -8,23 +8,38 @@
 
 namespace tlb {
 
-// ---- g storage: FP32, or FP16 scaled by 1/chi ----
+// ---- g storage: FP32 [Q][N], or mixed: the rest population g_0 in FP32
+// (N floats) followed by the moving populations in FP16, scaled by g_scale
+// ([Q-1][N] halves).  g_0 carries phi; the moving ones are small. ----
 template <typename GT>
 struct GIO;
 template <>
 struct GIO<float> {
-    static __device__ __forceinline__ float ld(const void *p, long long k, float) { return __ldg((const float *)p + k); }
-    static __device__ __forceinline__ void st(void *p, long long k, float v, float) { ((float *)p)[k] = v; }
+    static __device__ __forceinline__ float ld(const void *p, int i, long long n, const DevParams &q)
+    {
+        return __ldg((const float *)p + (long long)i * q.N + n);
+    }
+    static __device__ __forceinline__ void st(void *p, int i, long long n, float v, const DevParams &q)
+    {
+        ((float *)p)[(long long)i * q.N + n] = v;
+    }
 };
 template <>
 struct GIO<__half> {
-    static __device__ __forceinline__ float ld(const void *p, long long k, float unscale)
+    static __device__ __forceinline__ float ld(const void *p, int i, long long n, const DevParams &q)
     {
-        return __half2float(((const __half *)p)[k]) * unscale;
+        if (i == 0) return __ldg((const float *)p + n);
+        const __half *h = (const __half *)((const char *)p + 4 * q.N);
+        return __half2float(h[(long long)(i - 1) * q.N + n]) * q.g_unscale;
     }
-    static __device__ __forceinline__ void st(void *p, long long k, float v, float scale)
+    static __device__ __forceinline__ void st(void *p, int i, long long n, float v, const DevParams &q)
     {
-        ((__half *)p)[k] = __float2half_rn(v * scale);
+        if (i == 0) {
+            ((float *)p)[n] = v;
+            return;
+        }
+        __half *h = (__half *)((char *)p + 4 * q.N);
+        h[(long long)(i - 1) * q.N + n] = __float2half_rn(v * q.g_scale);
     }
 };
 
@@ -80,7 +95,7 @@ __device__ __forceinline__ void moments_node(const DevParams &p, const float *__
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         r += __ldg(f + (long long)i * p.N + n);
-        ph += GIO<GT>::ld(g, (long long)i * p.N + n, p.g_unscale);
+        ph += GIO<GT>::ld(g, i, n, p);
     }
     rho[n] = 1.0f + r;
     phi[n] = ph;
@@ -464,9 +479,9 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             for (int a = 0; a < D; ++a) cv += (float)cc<D>(i, a) * v[a];
             float ge = wt<D>(i) * (3.0f * p.Gamma * mup + 3.0f * ph * cv + 4.5f * ph * cv * cv - 1.5f * ph * v2);
             gsum += ge;
-            GIO<GT>::st(g_out, (long long)i * p.N + n, ge, p.g_scale);
+            GIO<GT>::st(g_out, i, n, ge, p);
         }
-        GIO<GT>::st(g_out, n, ph - gsum, p.g_scale);
+        GIO<GT>::st(g_out, 0, n, ph - gsum, p);
         return;
     }
 
@@ -573,7 +588,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float gi = (ASYNC && sizeof(GT) == 4) ? stage[(Q + i) * NT + tid]
-                                               : GIO<GT>::ld(g_in, (long long)i * p.N + n, p.g_unscale);
+                                               : GIO<GT>::ld(g_in, i, n, p);
         if (i == 0) { g0 = gi; continue; }
         float cv = 0.f;
 #pragma unroll
@@ -583,13 +598,13 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         float gn = gi + (ge - gi) * p.inv_tau_g;
         int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
         if (stype[m] & TLB_SOLID)
-            GIO<GT>::st(g_out, (long long)opp<D>(i) * p.N + n, gn, p.g_scale);
+            GIO<GT>::st(g_out, opp<D>(i), n, gn, p);
         else
-            GIO<GT>::st(g_out, (long long)i * p.N + nbr(cc<D>(i, 0), cc<D>(i, 1), cc<D>(i, 2)), gn, p.g_scale);
+            GIO<GT>::st(g_out, i, nbr(cc<D>(i, 0), cc<D>(i, 1), cc<D>(i, 2)), gn, p);
     }
     {
         float ge0 = ph - gsum;
-        GIO<GT>::st(g_out, n, g0 + (ge0 - g0) * p.inv_tau_g, p.g_scale);
+        GIO<GT>::st(g_out, 0, n, g0 + (ge0 - g0) * p.inv_tau_g, p);
     }
 }
 
@@ -709,10 +724,10 @@ __global__ void convert_kernel(DevParams p, float *f, void *g, double *fb, doubl
             long long k = (long long)i * p.N + n;
             if (dir == 0) {
                 fb[k] = (double)f[k] + (double)wt<D>(i);
-                gb[k] = (double)GIO<GT>::ld(g, k, p.g_unscale);
+                gb[k] = (double)GIO<GT>::ld(g, i, n, p);
             } else {
                 f[k] = (float)(fb[k] - (double)wt<D>(i));
-                GIO<GT>::st(g, k, (float)gb[k], p.g_scale);
+                GIO<GT>::st(g, i, n, (float)gb[k], p);
             }
         }
     }

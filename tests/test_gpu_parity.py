@@ -158,15 +158,19 @@ def test_d3q27_lubricated_small_1000_steps():
 
 
 def test_d3q27_fp16_order_parameter_error_is_bounded():
-    """FP16 storage of g (scaled by 1/chi) is a reduced-precision format; its
-    error against the FP64 oracle is bounded, not held to the FP32 bar."""
+    """Reduced-precision g storage (g_0 in FP32, moving populations in FP16
+    scaled by 16) is not held to the FP32 bar; its error against the FP64
+    oracle after 200 steps is reported and bounded by 1e-3 (normwise), the
+    accumulation of the FP16 rounding (2^-11 relative) of the moving
+    populations."""
     wl = _small3d(g_fp16=1)
     g = gpu_from_workload(wl)
     o = oracle_from_workload(wl)
     g.step(200)
     o.step(200)
     e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
-    assert e["phi"] < 2e-2 and e["rho"] < 2e-2, e
+    print("FP16 g storage, 200 steps, normwise error vs FP64 oracle:", e)
+    assert e["phi"] < 1e-3 and e["rho"] < 1e-3 and e["C"] < 1e-3, e
 
 
 def test_c2_full_size_first_steps_match():
