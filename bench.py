@@ -256,6 +256,30 @@ def run_ours(args):
             "roofline": roofline(lb.Q, lb.N, bkms, peak, peak_kind,
                                  "step_batch_kernel<D3Q27> (ghost layer, stencils, force, collision, stream)",
                                  big["name"])}
+        # reduced-precision g (rest population FP32, moving populations FP16)
+        big16 = dict(big)
+        big16["params"] = dict(big["params"], g_fp16=1)
+        l16 = tlb.lattice_from_workload(big16)
+        tlb.tlb_set_stream(l16.h, stream.cuda_stream)
+        hms, hkms, _, _ = measure(l16, stream, max(args.steps // 10, 10), 3, flush=None)
+        # same number of steps from the same initial state in both formats
+        n32, n16 = lb.steps_done, l16.steps_done
+        if n16 < n32:
+            l16.step(n32 - n16)
+        elif n32 < n16:
+            lb.step(n16 - n32)
+        f32, f16 = lb.fields(), l16.fields()
+        fl = big["mask"] == 0
+        d = lb.derived
+        result["large_lattice_fp16_g"] = {
+            "workload": big["name"] + " (g: g_0 FP32, moving populations FP16)",
+            "value": round(world * l16.N / (hms * 1e-3) / 1e6, 2), "unit": "MLUPS", "ms_per_step": round(hms, 4),
+            "kernel_ms": round(hkms, 5),
+            "normwise_diff_vs_fp32_after_steps": {
+                "steps": int(max(n32, n16)),
+                "rho": float(np.abs(f32["rho"] - f16["rho"])[fl].max() / (d["rho_l"] - d["rho_g"])),
+                "phi": float(np.abs(f32["phi"] - f16["phi"])[fl].max() / big["params"]["chi"])}}
+        l16.close()
         lb.close()
     if rank == 0 and not args.no_batch:
         result["batched"] = batched_sweep()
