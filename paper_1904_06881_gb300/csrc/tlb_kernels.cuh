@@ -76,7 +76,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int D, typename GT>
 __host__ __device__ constexpr int stage_bytes()
 {
-    return Lat<D>::Q * Tile<D>::X * Tile<D>::Y * Tile<D>::Z * 4 * (sizeof(GT) == 4 ? 2 : 1);
+    // f: Q floats; g: Q floats, or g_0 as a float plus Q-1 halves
+    return Tile<D>::X * Tile<D>::Y * Tile<D>::Z *
+           (Lat<D>::Q * 4 + (sizeof(GT) == 4 ? Lat<D>::Q * 4 : 4 + (Lat<D>::Q - 1) * 2));
 }
 
 // ---------------------------------------------------------------------------
@@ -291,6 +293,17 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
 #pragma unroll
                 for (int i = 0; i < Q; ++i)
                     cp_async4(&stage[(Q + i) * NT + tid], (const float *)g_in + (long long)i * p.N + an);
+            } else {
+                cp_async4(&stage[Q * NT + tid], (const float *)g_in + an);
+                // the FP16 moving populations of two x-neighbours share a 4-byte
+                // word (nx even): the even thread of each pair copies it
+                if ((p.nx & 1) == 0 && (tid & 1) == 0) {
+                    const char *h = (const char *)g_in + 4 * p.N;
+                    __half *s16 = reinterpret_cast<__half *>(&stage[(Q + 1) * NT]);
+#pragma unroll
+                    for (int i = 1; i < Q; ++i)
+                        cp_async4(&s16[(i - 1) * NT + tid], h + 2 * ((long long)(i - 1) * p.N + an));
+                }
             }
         }
         cp_async_commit();
@@ -343,10 +356,11 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         }
         smu[k] = t.mup;
     }
-    __syncthreads();
-
-    // every thread waits for its own staged copies before any thread can leave
+    // every thread's staged copies complete before the barrier, so each thread
+    // may read copies made by another (the FP16 pairs) and none is pending
+    // when a thread leaves
     if (ASYNC) cp_async_wait_all();
+    __syncthreads();
 
     // Stage C: one node per thread
     const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
@@ -587,8 +601,15 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     float gsum = 0.f, g0 = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float gi = (ASYNC && sizeof(GT) == 4) ? stage[(Q + i) * NT + tid]
-                                               : GIO<GT>::ld(g_in, i, n, p);
+        float gi;
+        if (ASYNC && sizeof(GT) == 4) {
+            gi = stage[(Q + i) * NT + tid];
+        } else if (ASYNC && (p.nx & 1) == 0) {
+            const __half *s16 = reinterpret_cast<const __half *>(&stage[(Q + 1) * NT]);
+            gi = (i == 0) ? stage[Q * NT + tid] : __half2float(s16[(i - 1) * NT + tid]) * p.g_unscale;
+        } else {
+            gi = GIO<GT>::ld(g_in, i, n, p);
+        }
         if (i == 0) { g0 = gi; continue; }
         float cv = 0.f;
 #pragma unroll
