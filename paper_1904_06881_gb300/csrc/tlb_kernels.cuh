@@ -62,6 +62,11 @@ __device__ __forceinline__ long long node_near(const DevParams &p, int x, int y,
     return (long long)wrap1(x, p.nx) + (long long)p.nx * ((long long)wrap1(y, p.ny) + (long long)p.ny * wrap1(z, p.nz));
 }
 
+// Programmatic dependent launch: a stepping kernel lets the next one be
+// scheduled at once and waits for its predecessor's results before reading.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // Asynchronous global -> shared copies (sm_80+ cp.async): the node's own
 // populations are requested before the tile stages and consumed after them.
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
@@ -114,6 +119,8 @@ __global__ void __launch_bounds__(256) moments_kernel(DevParams p, const float *
 template <int D, typename GT>
 __global__ void __launch_bounds__(256) moments_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
 {
+    pdl_trigger();
+    pdl_wait();
     int4 t = tiles[blockIdx.x];
     const BatchEntry &e = E[t.x];
     constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
@@ -646,6 +653,8 @@ template <int D, typename GT>
 __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
 {
     __shared__ BatchEntry se;
+    pdl_trigger();
+    pdl_wait();
     const int4 t = tiles[blockIdx.x];
     static_assert(sizeof(BatchEntry) % 4 == 0 && sizeof(BatchEntry) / 4 <= 256, "entry copy");
     if (threadIdx.x < sizeof(BatchEntry) / 4)
@@ -836,14 +845,31 @@ void Launch<D>::convert_pop(const DevParams &p, const DevState &s, int dir, doub
         convert_kernel<D, float><<<grid_for(p.N, 256), 256, 0, st>>>(p, s.f[s.cur], s.g[s.cur], fbuf, gbuf, dir);
 }
 
+// launch with programmatic stream serialization (the kernel's griddepcontrol.wait
+// orders it after its predecessor's memory operations)
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int D>
 void Launch<D>::moments_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st)
 {
     if (ntiles <= 0) return;
-    if (g_fp16)
-        moments_batch_kernel<D, __half><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
-    else
-        moments_batch_kernel<D, float><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, 0, st>>>(entries, tiles);
+    const int nt = Tile<D>::X * Tile<D>::Y * Tile<D>::Z;
+    if (g_fp16) launch_pdl(moments_batch_kernel<D, __half>, ntiles, nt, 0, st, entries, tiles);
+    else launch_pdl(moments_batch_kernel<D, float>, ntiles, nt, 0, st, entries, tiles);
 }
 
 template <int D, typename GT>
@@ -855,7 +881,7 @@ static void launch_step_batch(const BatchEntry *entries, const int4 *tiles, int 
         cudaFuncSetAttribute(step_batch_kernel<D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         attr = true;
     }
-    step_batch_kernel<D, GT><<<ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, bytes, st>>>(entries, tiles);
+    launch_pdl(step_batch_kernel<D, GT>, ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, (size_t)bytes, st, entries, tiles);
 }
 
 template <int D>
