@@ -137,15 +137,18 @@ def workload():
 
 
 def algorithmic_bytes(Q, N):
-    """Per launch of the fused step kernel: read f, g (Q floats each), write
-    f, g, read rho, phi (2 floats) and the node flag (1 byte) per node."""
-    return N * (16 * Q + 9)
+    """Per launch of the fused step kernel, per node: read f, g (Q floats
+    each), write f, g, read the node flag (1 byte); the D3Q27 kernel also
+    reads rho, phi (2 floats) from the moments pass (the D2Q9 kernel sums
+    them from the populations it reads)."""
+    return N * (16 * Q + (1 if Q == 9 else 9))
 
 
 def measure(lat, stream, steps, warmup, flush=None, kernel_steps=None):
     """Per-step time of whole steps (tlb_step: one CUDA graph of the step's
     launches) and the average duration of the fused step kernel alone (launched
-    through tlb_step_phase), both with CUDA events on the lattice's stream.
+    through tlb_step_phase; phase 0, the D3Q27 moments pass, is outside the
+    kernel's events), both with CUDA events on the lattice's stream.
     With `flush`, a buffer larger than L2 is written before every timed step."""
     import torch
 

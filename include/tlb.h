@@ -124,10 +124,12 @@ int tlb_init_fields_device(tlb_ctx *ctx, const float *rho, const float *phi, con
  * sticky error status seen by the last synchronising call. */
 int tlb_step(tlb_ctx *ctx, int nsteps);
 /* One phase of a time step, for per-kernel timing: phase 0 computes the
- * moments rho, phi; phase 1 is empty (kept for callers that issue 0, 1, 2);
- * phase 2 runs the fused kernel -- ghost layer, stencils, force, collision,
- * streaming -- and completes the step.  Issuing 0, 1, 2 (or 0, 2) in order is
- * exactly one tlb_step.  Asynchronous. */
+ * moments rho, phi (D3Q27; empty for D2Q9, whose step kernel sums the moments
+ * of its tile and halo itself); phase 1 is empty (kept for callers that issue
+ * 0, 1, 2); phase 2 runs the fused kernel -- ghost layer, stencils, force,
+ * collision, streaming -- and completes the step.  Issuing 0, 1, 2 (or 0, 2)
+ * in order is exactly one tlb_step.  A step is one launch (D2Q9) or two
+ * (D3Q27).  Asynchronous. */
 int tlb_step_phase(tlb_ctx *ctx, int phase);
 /* Wait for the context stream and report TLB_E_DIVERGED if a kernel flagged
  * a non-positive density or population since the last check. */

@@ -751,15 +751,19 @@ extern "C" int tlb_init_fields(tlb_ctx *c, const double *rho, const double *phi,
     return TLB_OK;
 }
 
-// The three launches of one step of a lattice, as a batch of one (the kernels
+// Launches of one step per lattice: D2Q9 one (the step kernel sums the
+// moments it needs), D3Q27 two (moments, step).
+static int launches_per_step(int D) { return D == 2 ? 1 : 2; }
+
+// The launches of one step of a lattice, as a batch of one (the kernels
 // tlb_step_batch uses, so alone and batched results are bit-identical).
+// Phase 0 is the moments pass (D3Q27 only), phase 2 the step kernel.
 static void issue_phase(tlb_ctx *c, int phase, cudaStream_t st)
 {
     const BatchEntry *E = c->self_entries + c->s.cur;
     int fp16 = c->p.g_fp16;
     if (c->D == 2) {
-        if (phase == 0) Launch<2>::moments_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
-        else if (phase == 2) Launch<2>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
+        if (phase == 2) Launch<2>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
     } else {
         if (phase == 0) Launch<3>::moments_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
         else if (phase == 2) Launch<3>::step_batch(E, c->self_tiles, c->nself_tiles, fp16, st);
@@ -772,7 +776,7 @@ static void issue_step_on(tlb_ctx *c, cudaStream_t st)
     issue_phase(c, 2, st);
 }
 
-// Capture the three launches of a step for the current buffer parity.
+// Capture the launches of a step for the current buffer parity.
 static int capture_step(tlb_ctx *c)
 {
     int par = c->s.cur;
@@ -796,7 +800,7 @@ extern "C" int tlb_step(tlb_ctx *c, int nsteps)
 {
     if (!c) return fail(TLB_E_INVAL, "null context");
     if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
-    const int per = 2;
+    const int per = launches_per_step(c->D);
     for (int k = 0; k < nsteps; ++k) {
         int rc = capture_step(c);
         if (rc) return rc;
@@ -815,6 +819,7 @@ extern "C" int tlb_step_phase(tlb_ctx *c, int phase)
     if (!c) return fail(TLB_E_INVAL, "null context");
     if (phase < 0 || phase > 2) return fail(TLB_E_INVAL, "phase must be 0, 1 or 2");
     if (phase == 1) return TLB_OK;        // the ghost layer is filled inside phase 2
+    if (phase == 0 && c->D == 2) return TLB_OK;   // D2Q9 step kernels sum their moments
     issue_phase(c, phase, c->stream);
     if (phase == 2) {
         c->s.cur ^= 1;
@@ -1083,7 +1088,6 @@ static int run_plan(BatchPlan &plan, int nsteps, cudaStream_t st)
         const BatchEntry *E = plan.entries[s & 1];
         int fp16 = plan.ctxs[0]->p.g_fp16;
         if (D == 2) {
-            Launch<2>::moments_batch(E, plan.tiles, plan.ntiles, fp16, st);
             Launch<2>::step_batch(E, plan.tiles, plan.ntiles, fp16, st);
         } else {
             Launch<3>::moments_batch(E, plan.tiles, plan.ntiles, fp16, st);
@@ -1092,7 +1096,7 @@ static int run_plan(BatchPlan &plan, int nsteps, cudaStream_t st)
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(TLB_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
-    const int per = 2;
+    const int per = launches_per_step(D);
     for (tlb_ctx *c : plan.ctxs) {
         if (nsteps & 1) c->s.cur ^= 1;
         c->steps += nsteps;

@@ -146,11 +146,12 @@ __device__ __forceinline__ Fac eq_factors(float u)
 
 __device__ __forceinline__ float fac_of(const Fac &f, int c) { return c == 0 ? f.f0 : (c > 0 ? f.fp : f.fm); }
 
-// phi(y) = (1 + y) ln(1 + y) - y, accurate for small |y| (series y^2/2 - y^3/6 + ...)
-__device__ __forceinline__ float phi_ent(float y)
+// phi(y) = (1 + y) ln(1 + y) - y given l = ln(1 + y), accurate for small |y|
+// (series y^2/2 - y^3/6 + ...)
+__device__ __forceinline__ float phi_ent(float y, float l)
 {
     if (fabsf(y) < 1e-2f) return y * y * (0.5f + y * (-1.0f / 6.0f + y * (1.0f / 12.0f - y * (1.0f / 20.0f))));
-    return (1.0f + y) * log1pf(y) - y;
+    return (1.0f + y) * l - y;
 }
 
 // Entropic alpha: the non-trivial root of H(f' + alpha D) = H(f')
@@ -194,23 +195,25 @@ __device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float 
     float L[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) L[i] = log1pf(x[i]);
-    auto hval = [&](float a, float &dh) {
-        float h = 0.f;
-        dh = 0.f;
+    float lo = 1.0f, hi = amax * (1.0f - 1e-6f);
+    if (!(al > lo && al < hi)) al = 0.5f * (lo + hi);
+    // iteration -1 (only when alpha_max < 4) evaluates h at the positivity
+    // bound: h < 0 there means no root below it.  One copy of the h, h' loop.
+#pragma unroll 1
+    for (int it = hi < 4.0f ? -1 : 0; it < 16; ++it) {
+        const float a = it < 0 ? hi : al;
+        float h = 0.f, dh = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            float y = a * x[i];
-            h += fp[i] * (phi_ent(y) - y * L[i]);
-            dh += fp[i] * x[i] * (log1pf(y) - L[i]);
+            const float y = a * x[i];
+            const float ly = log1pf(y);
+            h += fp[i] * (phi_ent(y, ly) - y * L[i]);
+            dh += fp[i] * x[i] * (ly - L[i]);
         }
-        return h;
-    };
-    float lo = 1.0f, hi = amax * (1.0f - 1e-6f);
-    float dh;
-    if (hi < 4.0f && hval(hi, dh) < 0.f) return hi;      // no root below the positivity bound
-    if (!(al > lo && al < hi)) al = 0.5f * (lo + hi);
-    for (int it = 0; it < 16; ++it) {
-        float h = hval(al, dh);
+        if (it < 0) {
+            if (h < 0.f) return hi;
+            continue;
+        }
         if (h > 0.f) hi = al; else lo = al;
         if (dh > 0.f) {
             float step = (float)((double)h / (double)dh);
@@ -237,17 +240,31 @@ __device__ __forceinline__ bool is_fluid(const uint8_t *type, long long n)
     return !(type[n] & TLB_SOLID);
 }
 
-template <int D>
-__device__ void ghost_axis(const DevParams &p, const uint8_t *__restrict__ type, const float *__restrict__ rho,
-                           const float *__restrict__ phi, int yx, int yy, int yz, int axis, float &gr, float &gp)
+// Moments (rho, phi) of a fluid node read from the arrays the moments kernel
+// writes.  A moment accessor is called with the node's coordinates (not
+// wrapped: they may lie up to a few nodes outside the lattice) and its index.
+struct MomArrays {
+    const float *rho, *phi;
+    __device__ __forceinline__ float2 operator()(int, int, int, long long n) const
+    {
+        return make_float2(rho[n], phi[n]);
+    }
+};
+
+// The ghost value of one fluid-facing axis direction: (yx, yy, yz) is the
+// first fluid node along `axis`; `mom` gives (rho, phi) of fluid nodes.
+template <int D, class M>
+__device__ void ghost_axis(const DevParams &p, const uint8_t *__restrict__ type, const M &mom, int yx, int yy, int yz,
+                           int axis, float &gr, float &gp)
 {
     long long y = node_of(p, yx, yy, yz);
-    float r1 = rho[y], p1 = phi[y];
+    const float2 m1 = mom(yx, yy, yz, y);
+    float r1 = m1.x, p1 = m1.y;
     if (p.wetting == TLB_WET_FORCE) { gr = r1; gp = p1; return; }
+    constexpr int nt = D - 1;                 // in-plane axes
     int T[2];
-    int nt = 0;
-    for (int t = 0; t < D; ++t)
-        if (t != axis) T[nt++] = t;
+    T[0] = axis == 0 ? 1 : 0;
+    T[1] = axis == 2 ? 1 : 2;
     float dr[2] = {0.f, 0.f}, dp[2] = {0.f, 0.f};
     int yc[3] = {yx, yy, yz};
     for (int k = 0; k < nt; ++k) {
@@ -256,9 +273,19 @@ __device__ void ghost_axis(const DevParams &p, const uint8_t *__restrict__ type,
         cm[T[k]] -= 1;
         long long np_ = node_of(p, cp[0], cp[1], cp[2]), nm = node_of(p, cm[0], cm[1], cm[2]);
         bool fp_ = is_fluid<D>(type, np_), fm = is_fluid<D>(type, nm);
-        if (fp_ && fm) { dr[k] = 0.5f * (rho[np_] - rho[nm]); dp[k] = 0.5f * (phi[np_] - phi[nm]); }
-        else if (fp_) { dr[k] = rho[np_] - r1; dp[k] = phi[np_] - p1; }
-        else if (fm) { dr[k] = r1 - rho[nm]; dp[k] = p1 - phi[nm]; }
+        if (fp_ && fm) {
+            const float2 a = mom(cp[0], cp[1], cp[2], np_), b = mom(cm[0], cm[1], cm[2], nm);
+            dr[k] = 0.5f * (a.x - b.x);
+            dp[k] = 0.5f * (a.y - b.y);
+        } else if (fp_) {
+            const float2 a = mom(cp[0], cp[1], cp[2], np_);
+            dr[k] = a.x - r1;
+            dp[k] = a.y - p1;
+        } else if (fm) {
+            const float2 b = mom(cm[0], cm[1], cm[2], nm);
+            dr[k] = r1 - b.x;
+            dp[k] = p1 - b.y;
+        }
     }
     float nr = 0.f, npp = 0.f, dot = 0.f;
     for (int k = 0; k < nt; ++k) { nr += dr[k] * dr[k]; npp += dp[k] * dp[k]; dot += dr[k] * dp[k]; }
@@ -290,8 +317,14 @@ __device__ void ghost_axis(const DevParams &p, const uint8_t *__restrict__ type,
         q[T[0]] += k1;
         if (nt > 1) q[T[1]] += k2;
         long long m = node_of(p, q[0], q[1], q[2]);
-        if (is_fluid<D>(type, m)) { vr = rho[m]; vp = phi[m]; }
-        else { vr = r1; vp = p1; }
+        if (is_fluid<D>(type, m)) {
+            const float2 a = mom(q[0], q[1], q[2], m);
+            vr = a.x;
+            vp = a.y;
+        } else {
+            vr = r1;
+            vp = p1;
+        }
     };
     if (nt == 1) {
         float l = cot * tx;

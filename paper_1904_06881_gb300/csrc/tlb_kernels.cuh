@@ -89,6 +89,21 @@ __host__ __device__ constexpr int stage_bytes()
 // ---------------------------------------------------------------------------
 // moments: rho = 1 + sum_i (f_i - w_i), phi = sum_i g_i at fluid nodes
 // ---------------------------------------------------------------------------
+// Out of line: called from several places of the ghost-layer code, whose
+// inlined copies would multiply the stepping kernel's instruction footprint.
+template <int D, typename GT>
+__device__ __noinline__ float2 pop_moments(const DevParams &p, const float *__restrict__ f, const void *g, long long n)
+{
+    constexpr int Q = Lat<D>::Q;
+    float r = 0.f, ph = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        r += __ldg(f + (long long)i * p.N + n);
+        ph += GIO<GT>::ld(g, i, n, p);
+    }
+    return make_float2(1.0f + r, ph);
+}
+
 template <int D, typename GT>
 __device__ __forceinline__ void moments_node(const DevParams &p, const float *__restrict__ f, const void *g,
                                              const uint8_t *__restrict__ type, float *rho, float *phi, long long n)
@@ -98,14 +113,9 @@ __device__ __forceinline__ void moments_node(const DevParams &p, const float *__
         if (!(type[n] & TLB_GHOST)) { rho[n] = 0.f; phi[n] = 0.f; }
         return;
     }
-    float r = 0.f, ph = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        r += __ldg(f + (long long)i * p.N + n);
-        ph += GIO<GT>::ld(g, i, n, p);
-    }
-    rho[n] = 1.0f + r;
-    phi[n] = ph;
+    const float2 m = pop_moments<D, GT>(p, f, g, n);
+    rho[n] = m.x;
+    phi[n] = m.y;
 }
 
 template <int D, typename GT>
@@ -135,34 +145,38 @@ __global__ void __launch_bounds__(256) moments_batch_kernel(const BatchEntry *__
 // ghost layer (Sec. IV): average over fluid-facing axis directions; ghosts
 // with only diagonal fluid neighbours take the mean of those neighbours.
 // ---------------------------------------------------------------------------
-template <int D>
-__device__ void ghost_value(const DevParams &p, const uint8_t *__restrict__ type, const float *rho, const float *phi,
-                            long long n, float &gr_out, float &gp_out)
+template <int D, class M>
+__device__ void ghost_value(const DevParams &p, const uint8_t *__restrict__ type, const M &mom, int x, int y, int z,
+                            float &gr_out, float &gp_out)
 {
     constexpr int Q = Lat<D>::Q;
-    int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
     int c[3] = {x, y, z};
     float sr = 0.f, sp = 0.f;
     int cnt = 0;
+    // one copy of the (large) axis code, not one per direction
+#pragma unroll 1
     for (int a = 0; a < D; ++a)
+#pragma unroll 1
         for (int s = -1; s <= 1; s += 2) {
             int q[3] = {c[0], c[1], c[2]};
             q[a] += s;
             long long m = node_of(p, q[0], q[1], q[2]);
             if (type[m] & TLB_SOLID) continue;
             float gr, gp;
-            ghost_axis<D>(p, type, rho, phi, wrapi(q[0], p.nx), wrapi(q[1], p.ny), wrapi(q[2], p.nz), a, gr, gp);
+            ghost_axis<D>(p, type, mom, q[0], q[1], q[2], a, gr, gp);
             sr += gr;
             sp += gp;
             ++cnt;
         }
     if (cnt == 0) {
-#pragma unroll
+#pragma unroll 1
         for (int i = 1; i < Q; ++i) {
-            long long m = node_of(p, x + cc<D>(i, 0), y + cc<D>(i, 1), z + cc<D>(i, 2));
+            const int qx = x + cc<D>(i, 0), qy = y + cc<D>(i, 1), qz = z + cc<D>(i, 2);
+            long long m = node_of(p, qx, qy, qz);
             if (type[m] & TLB_SOLID) continue;
-            sr += rho[m];
-            sp += phi[m];
+            const float2 a = mom(qx, qy, qz, m);
+            sr += a.x;
+            sp += a.y;
             ++cnt;
         }
     }
@@ -174,7 +188,8 @@ template <int D>
 __device__ void ghost_node(const DevParams &p, const uint8_t *__restrict__ type, float *rho, float *phi, long long n)
 {
     float gr, gp;
-    ghost_value<D>(p, type, rho, phi, n, gr, gp);
+    const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
+    ghost_value<D>(p, type, MomArrays{rho, phi}, x, y, z, gr, gp);
     rho[n] = gr;
     phi[n] = gp;
 }
@@ -266,10 +281,38 @@ __device__ __forceinline__ int qcomp(int a, int b)
     return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
 }
 
+// Moments of a fluid node for the ghost layer when a tile sums its own
+// moments: from the tile + halo-2 region in shared memory when the node lies
+// there, else summed from the node's populations.  (ox, oy, oz) is the
+// region's first node; region slots at or beyond n + 2 along an axis are not
+// filled and are not read.
+template <int D, typename GT, int RX, int RY, int RZ>
+struct MomTile {
+    const DevParams &p;
+    const float *f;
+    const void *g;
+    const float *srho, *sphi;
+    int ox, oy, oz;
+    __device__ __forceinline__ float2 operator()(int x, int y, int z, long long n) const
+    {
+        const int lx = x - ox, ly = y - oy, lz = z - oz;
+        if ((unsigned)lx < (unsigned)RX && (unsigned)ly < (unsigned)RY && (unsigned)lz < (unsigned)RZ &&
+            x < p.nx + 2 && y < p.ny + 2 && z < p.nz + 2) {
+            const int k = lx + RX * (ly + RY * lz);
+            return make_float2(srho[k], sphi[k]);
+        }
+        return pop_moments<D, GT>(p, f, g, n);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // The fused step kernel.  One CTA = one tile of TX x TY x TZ nodes.
+// ASYNC: the node's own populations are staged by cp.async before stage A.
+// FUSED (D2Q9): stage A sums rho, phi of the tile + halo 2 from the
+// populations itself (no moments pass before the step) and keeps the tile's
+// own populations in shared memory.
 // ---------------------------------------------------------------------------
-template <int D, typename GT, int MODE, bool ASYNC = false>
+template <int D, typename GT, int MODE, bool ASYNC = false, bool FUSED = false>
 __device__ __forceinline__ void step_tile(const DevParams &p, const float *__restrict__ f_in, float *__restrict__ f_out,
                                           const void *g_in, void *g_out, const float *__restrict__ rho,
                                           const float *__restrict__ phi, const uint8_t *__restrict__ type,
@@ -316,25 +359,132 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         cp_async_commit();
     }
 
-    // Stage A: rho, phi of the tile + halo 2, the ghost layer of Sec. IV filled
-    // here from the fluid moments (the moments pass leaves ghost nodes alone);
-    // node flags of the tile + halo 1
-    for (int k = tid; k < NR; k += blockDim.x) {
-        int lx = k % RX, ly = (k / RX) % RY, lz = k / (RX * RY);
-        long long n = node_near(p, x0 - 2 + lx, y0 - 2 + ly, z0 - HZ2 + lz);
-        if (__ldg(type + n) & TLB_GHOST) {
-            float gr, gp;
-            ghost_value<D>(p, type, rho, phi, n, gr, gp);
-            srho[k] = gr;
-            sphi[k] = gp;
-        } else {
-            srho[k] = __ldg(rho + n);
-            sphi[k] = __ldg(phi + n);
+    // Region slots are filled for coordinates below n + 2 (n + 1 for the flags)
+    // along each axis: the tile's nodes use no farther neighbours, and
+    // node_near wraps one period only.
+    if constexpr (FUSED) {
+        static_assert(D == 2 && !ASYNC, "summed moments: D2Q9 tiles");
+        // Stage A1: thread tid sums its own node (tile slot tid) and, for
+        // tid < NR - NT, one node of the halo ring: rows 0-1 and RY-2..RY-1,
+        // then the two columns on either side of rows 2..RY-3.
+        constexpr int NH = NR - NT;
+        static_assert(NH == 4 * RX + 4 * TY && NT == 256, "halo ring of a 32 x 8 tile");
+        int kl[2], kx[2], ky[2];
+        kx[0] = 2 + tid % TX;
+        ky[0] = 2 + tid / TX;
+        const bool has_h = tid < NH;
+        {
+            const int h = has_h ? tid : 0;
+            if (h < 2 * RX) { kx[1] = h % RX; ky[1] = h / RX; }
+            else if (h < 4 * RX) { kx[1] = (h - 2 * RX) % RX; ky[1] = RY - 2 + (h - 2 * RX) / RX; }
+            else {
+                const int c = (h - 4 * RX) & 3;
+                kx[1] = c < 2 ? c : TX + c;
+                ky[1] = 2 + ((h - 4 * RX) >> 2);
+            }
+        }
+        float fa[2][Q], ga[2][Q];
+        __half gh[2][Q];                     // FP16 storage: the raw moving populations
+        long long na[2];
+        bool in[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            kl[s] = kx[s] + RX * ky[s];
+            const int X = x0 - 2 + kx[s], Y = y0 - 2 + ky[s];
+            in[s] = (s == 0 || has_h) && X < p.nx + 2 && Y < p.ny + 2;
+            na[s] = in[s] ? node_near(p, X, Y, 0) : 0;
+        }
+        // issue both nodes' loads before any sum
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                fa[s][i] = in[s] ? __ldg(f_in + (long long)i * p.N + na[s]) : 0.f;
+                if (sizeof(GT) == 4 || i == 0) {
+                    ga[s][i] = in[s] ? GIO<float>::ld(g_in, i, na[s], p) : 0.f;
+                } else {
+                    // the value GIO<__half>::ld returns, from one load of the raw half
+                    const __half *hb = (const __half *)((const char *)g_in + 4 * p.N);
+                    gh[s][i] = in[s] ? hb[(long long)(i - 1) * p.N + na[s]] : __float2half_rn(0.f);
+                    ga[s][i] = __half2float(gh[s][i]) * p.g_unscale;
+                }
+            }
+        if (x0 + kx[0] - 2 < p.nx && y0 + ky[0] - 2 < p.ny) {
+            // the node's own populations for stage C, in the staging layout
+#pragma unroll
+            for (int i = 0; i < Q; ++i) stage[i * NT + tid] = fa[0][i];
+            if (sizeof(GT) == 4) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) stage[(Q + i) * NT + tid] = ga[0][i];
+            } else {
+                stage[Q * NT + tid] = ga[0][0];
+                __half *s16 = reinterpret_cast<__half *>(&stage[(Q + 1) * NT]);
+#pragma unroll
+                for (int i = 1; i < Q; ++i) s16[(i - 1) * NT + tid] = gh[0][i];
+            }
+        }
+        bool ghost = false;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s == 1 && !has_h) break;
+            float r = 0.f, ph = 0.f;
+            if (in[s]) {
+                const uint8_t t = __ldg(type + na[s]);
+                ghost |= (t & TLB_GHOST) != 0;
+                if (!(t & TLB_SOLID)) {
+                    // the summation order of the moments kernel
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        r += fa[s][i];
+                        ph += ga[s][i];
+                    }
+                    r = 1.0f + r;
+                }
+            }
+            srho[kl[s]] = r;
+            sphi[kl[s]] = ph;
+        }
+        // Stage A2: the ghost layer of Sec. IV from the fluid moments
+        if (__syncthreads_or(ghost)) {
+            const MomTile<D, GT, RX, RY, RZ> mom{p, f_in, g_in, srho, sphi, x0 - 2, y0 - 2, 0};
+            for (int k = tid; k < NR; k += blockDim.x) {
+                const int X = x0 - 2 + k % RX, Y = y0 - 2 + k / RX;
+                if (X >= p.nx + 2 || Y >= p.ny + 2) continue;
+                if (!(__ldg(type + node_near(p, X, Y, 0)) & TLB_GHOST)) continue;
+                float gr, gp;
+                ghost_value<D>(p, type, mom, X, Y, 0, gr, gp);
+                srho[k] = gr;
+                sphi[k] = gp;
+            }
+        }
+    } else {
+        // Stage A: rho, phi of the tile + halo 2, the ghost layer of Sec. IV
+        // filled here from the fluid moments (the moments pass leaves ghost
+        // nodes alone)
+        for (int k = tid; k < NR; k += blockDim.x) {
+            const int X = x0 - 2 + k % RX, Y = y0 - 2 + (k / RX) % RY, Z = z0 - HZ2 + k / (RX * RY);
+            if (X >= p.nx + 2 || Y >= p.ny + 2 || Z >= p.nz + 2) {
+                srho[k] = 0.f;
+                sphi[k] = 0.f;
+                continue;
+            }
+            long long n = node_near(p, X, Y, Z);
+            if (__ldg(type + n) & TLB_GHOST) {
+                float gr, gp;
+                ghost_value<D>(p, type, MomArrays{rho, phi}, X, Y, Z, gr, gp);
+                srho[k] = gr;
+                sphi[k] = gp;
+            } else {
+                srho[k] = __ldg(rho + n);
+                sphi[k] = __ldg(phi + n);
+            }
         }
     }
+    // node flags of the tile + halo 1
     for (int k = tid; k < NS; k += blockDim.x) {
-        int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
-        stype[k] = __ldg(type + node_near(p, x0 - 1 + lx, y0 - 1 + ly, z0 - HZ1 + lz));
+        const int X = x0 - 1 + k % SX, Y = y0 - 1 + (k / SX) % SY, Z = z0 - HZ1 + k / (SX * SY);
+        stype[k] = (X >= p.nx + 1 || Y >= p.ny + 1 || Z >= p.nz + 1) ? (uint8_t)TLB_SOLID
+                                                                      : __ldg(type + node_near(p, X, Y, Z));
     }
     __syncthreads();
 
@@ -512,7 +662,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float fi = ASYNC ? stage[i * NT + tid] : __ldg(f_in + (long long)i * p.N + n);
+        float fi = (ASYNC || FUSED) ? stage[i * NT + tid] : __ldg(f_in + (long long)i * p.N + n);
         fp[i] = fi;
 #pragma unroll
         for (int a = 0; a < D; ++a)
@@ -609,9 +759,9 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float gi;
-        if (ASYNC && sizeof(GT) == 4) {
+        if ((ASYNC || FUSED) && sizeof(GT) == 4) {
             gi = stage[(Q + i) * NT + tid];
-        } else if (ASYNC && (p.nx & 1) == 0) {
+        } else if (FUSED || (ASYNC && (p.nx & 1) == 0)) {
             const __half *s16 = reinterpret_cast<const __half *>(&stage[(Q + 1) * NT]);
             gi = (i == 0) ? stage[Q * NT + tid] : __half2float(s16[(i - 1) * NT + tid]) * p.g_unscale;
         } else {
@@ -650,7 +800,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_kernel(DevParams p, 
 // a tile table (lattice index, tile origin).  A lattice advanced alone is a
 // batch of one, so its results are bit-identical to the same lattice in a mix.
 template <int D, typename GT>
-__global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
+__global__ void __launch_bounds__(256, D == 2 ? 3 : 2) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
 {
     __shared__ BatchEntry se;
     pdl_trigger();
@@ -661,8 +811,9 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_batch_kernel(const B
         reinterpret_cast<int *>(&se)[threadIdx.x] = reinterpret_cast<const int *>(&E[t.x])[threadIdx.x];
     __syncthreads();
     AuxOut none = {};
-    step_tile<D, GT, MODE_STEP, true>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type, se.status,
-                                      t.y, t.z, t.w, nullptr, none);
+    // D2Q9 tiles sum their own moments; D3Q27 tiles read those of the moments kernel
+    step_tile<D, GT, MODE_STEP, D == 3, D == 2>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type,
+                                                se.status, t.y, t.z, t.w, nullptr, none);
 }
 
 // ---------------------------------------------------------------------------
