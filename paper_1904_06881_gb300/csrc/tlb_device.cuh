@@ -160,14 +160,15 @@ __device__ __forceinline__ float phi_ent(float y, float l)
 // ln(f^eq_i(u+du)/w_i) is affine in c_i,
 //   h(alpha) = sum_i f'_i [ phi(alpha x_i) - alpha x_i ln(1 + x_i) ],
 //   h'(alpha) = sum_i f'_i x_i [ ln(1 + alpha x_i) - ln(1 + x_i) ],
+//   h''(alpha) = sum_i f'_i x_i^2 / (1 + alpha x_i),
 // which involves no difference of O(1) entropies.  Expanding h/alpha in x
 // with the moments a_k = sum_i f'_i x_i^k and solving alpha = 2 + e1 + e2 + e3
 // order by order gives
 //   e1 = a3 / (3 a2),  e2 = 2 (2 a3^2 - 3 a2 a4) / (9 a2^2),
 //   e3 = (297 a2^2 a5 - 420 a2 a3 a4 + 170 a3^3) / (270 a2^3),
 // used as is up to max|x| = 0.03 (its effect on f stays below 1e-8 there) and as
-// the start of Newton's method, bracketed by [1, alpha_max), above it (nodes
-// at the interface); there the ratio h/h' of each Newton step is taken in FP64.
+// the start of Halley's method (third order, from h, h', h''), bracketed by
+// [1, alpha_max), above it (nodes at the interface).
 template <int Q>
 __device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&x)[Q])
 {
@@ -189,77 +190,94 @@ __device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float 
     return 2.0f + e1 + e2 + e3;
 }
 
+// Root of h in (1, alpha_max) from the start al.  h(1) < 0 always; when h is
+// still negative at the positivity bound there is no root below it and the
+// bound is returned.  h is evaluated at the bound only when an update would
+// cross it.  An update of at most 1e-3 alpha is applied and ends the
+// iteration: the third-order convergence leaves an error of order 1e-9
+// alpha, below the FP32 evaluation noise of h (about 1e-6 alpha at
+// max|x| = 0.5).
 template <int Q>
 __device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float (&x)[Q], float amax, float al)
 {
     float L[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) L[i] = log1pf(x[i]);
-    float lo = 1.0f, hi = amax * (1.0f - 1e-6f);
+    const float bound = amax * (1.0f - 1e-6f);
+    float lo = 1.0f, hi = bound;
+    bool probed = false;
     if (!(al > lo && al < hi)) al = 0.5f * (lo + hi);
-    // iteration -1 (only when alpha_max < 4) evaluates h at the positivity
-    // bound: h < 0 there means no root below it.  One copy of the h, h' loop.
+    float a = al;
 #pragma unroll 1
-    for (int it = hi < 4.0f ? -1 : 0; it < 16; ++it) {
-        const float a = it < 0 ? hi : al;
-        float h = 0.f, dh = 0.f;
+    for (int it = 0; it < 20; ++it) {
+        // the terms of h, h', h'' are independent: unrolled for instruction-level parallelism
+        float h = 0.f, d1 = 0.f, d2 = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const float y = a * x[i];
             const float ly = log1pf(y);
             h += fp[i] * (phi_ent(y, ly) - y * L[i]);
-            dh += fp[i] * x[i] * (ly - L[i]);
+            d1 += fp[i] * x[i] * (ly - L[i]);
+            d2 += fp[i] * x[i] * x[i] / (1.0f + y);
         }
-        if (it < 0) {
-            if (h < 0.f) return hi;
+        if (a == bound) {
+            if (h < 0.f) return bound;        // no root below the positivity bound
+            probed = true;                    // the bound brackets the root: bisect
+            a = 0.5f * (lo + hi);
             continue;
         }
+        al = a;
         if (h > 0.f) hi = al; else lo = al;
-        if (dh > 0.f) {
-            float step = (float)((double)h / (double)dh);
-            if (fabsf(step) <= 1e-6f * al) {   // converged: accept the last Newton step
-                al -= step;
-                break;
+        float nxt;
+        if (d1 > 0.f) {
+            const float s = h / d1;
+            const float step = s / (1.0f - 0.5f * s * d2 / d1);   // Halley's update
+            if (fabsf(step) <= 1e-3f * al) return fminf(al - step, bound);
+            nxt = al - step;
+            if (!(nxt > lo && nxt < hi)) {
+                if (nxt >= hi && hi == bound && !probed) {
+                    a = bound;
+                    continue;
+                }
+                nxt = 0.5f * (lo + hi);
             }
-            float nxt = al - step;
-            al = (nxt > lo && nxt < hi) ? nxt : 0.5f * (lo + hi);
         } else {
-            al = 0.5f * (lo + hi);
+            nxt = 0.5f * (lo + hi);
         }
-        if (hi - lo <= 2e-6f * hi) break;
+        if (hi - lo <= 2e-6f * hi) return nxt;
+        a = nxt;
     }
-    return al;
+    return a;
 }
 
 // ---------------------------------------------------------------------------
 // Ghost layer (Sec. IV): one fluid-facing direction of a ghost node.
 // ---------------------------------------------------------------------------
-template <int D>
-__device__ __forceinline__ bool is_fluid(const uint8_t *type, long long n)
-{
-    return !(type[n] & TLB_SOLID);
-}
-
-// Moments (rho, phi) of a fluid node read from the arrays the moments kernel
-// writes.  A moment accessor is called with the node's coordinates (not
-// wrapped: they may lie up to a few nodes outside the lattice) and its index.
-struct MomArrays {
+// A node accessor answers, for a node given by coordinates that are not
+// wrapped (they may lie a few nodes outside the lattice), whether it is a
+// fluid node and, if so, its moments (rho, phi).
+//
+// NodesGlobal: node flags and the moment arrays the moments kernel writes.
+struct NodesGlobal {
+    const DevParams &p;
+    const uint8_t *type;
     const float *rho, *phi;
-    __device__ __forceinline__ float2 operator()(int, int, int, long long n) const
+    __device__ __forceinline__ bool get(int x, int y, int z, float2 &m) const
     {
-        return make_float2(rho[n], phi[n]);
+        const long long n = node_of(p, x, y, z);
+        if (type[n] & TLB_SOLID) return false;
+        m = make_float2(rho[n], phi[n]);
+        return true;
     }
 };
 
 // The ghost value of one fluid-facing axis direction: (yx, yy, yz) is the
-// first fluid node along `axis`; `mom` gives (rho, phi) of fluid nodes.
-template <int D, class M>
-__device__ void ghost_axis(const DevParams &p, const uint8_t *__restrict__ type, const M &mom, int yx, int yy, int yz,
-                           int axis, float &gr, float &gp)
+// first fluid node along `axis`, m1 its moments; `acc` a node accessor.
+template <int D, class A>
+__device__ void ghost_axis(const DevParams &p, const A &acc, int yx, int yy, int yz, int axis, float2 m1, float &gr,
+                           float &gp)
 {
-    long long y = node_of(p, yx, yy, yz);
-    const float2 m1 = mom(yx, yy, yz, y);
-    float r1 = m1.x, p1 = m1.y;
+    const float r1 = m1.x, p1 = m1.y;
     if (p.wetting == TLB_WET_FORCE) { gr = r1; gp = p1; return; }
     constexpr int nt = D - 1;                 // in-plane axes
     int T[2];
@@ -267,22 +285,20 @@ __device__ void ghost_axis(const DevParams &p, const uint8_t *__restrict__ type,
     T[1] = axis == 2 ? 1 : 2;
     float dr[2] = {0.f, 0.f}, dp[2] = {0.f, 0.f};
     int yc[3] = {yx, yy, yz};
+#pragma unroll
     for (int k = 0; k < nt; ++k) {
         int cp[3] = {yc[0], yc[1], yc[2]}, cm[3] = {yc[0], yc[1], yc[2]};
         cp[T[k]] += 1;
         cm[T[k]] -= 1;
-        long long np_ = node_of(p, cp[0], cp[1], cp[2]), nm = node_of(p, cm[0], cm[1], cm[2]);
-        bool fp_ = is_fluid<D>(type, np_), fm = is_fluid<D>(type, nm);
+        float2 a, b;
+        const bool fp_ = acc.get(cp[0], cp[1], cp[2], a), fm = acc.get(cm[0], cm[1], cm[2], b);
         if (fp_ && fm) {
-            const float2 a = mom(cp[0], cp[1], cp[2], np_), b = mom(cm[0], cm[1], cm[2], nm);
             dr[k] = 0.5f * (a.x - b.x);
             dp[k] = 0.5f * (a.y - b.y);
         } else if (fp_) {
-            const float2 a = mom(cp[0], cp[1], cp[2], np_);
             dr[k] = a.x - r1;
             dp[k] = a.y - p1;
         } else if (fm) {
-            const float2 b = mom(cm[0], cm[1], cm[2], nm);
             dr[k] = r1 - b.x;
             dp[k] = p1 - b.y;
         }
@@ -316,9 +332,8 @@ __device__ void ghost_axis(const DevParams &p, const uint8_t *__restrict__ type,
         int q[3] = {yc[0], yc[1], yc[2]};
         q[T[0]] += k1;
         if (nt > 1) q[T[1]] += k2;
-        long long m = node_of(p, q[0], q[1], q[2]);
-        if (is_fluid<D>(type, m)) {
-            const float2 a = mom(q[0], q[1], q[2], m);
+        float2 a;
+        if (acc.get(q[0], q[1], q[2], a)) {
             vr = a.x;
             vp = a.y;
         } else {

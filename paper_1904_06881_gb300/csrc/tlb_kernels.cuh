@@ -89,10 +89,8 @@ __host__ __device__ constexpr int stage_bytes()
 // ---------------------------------------------------------------------------
 // moments: rho = 1 + sum_i (f_i - w_i), phi = sum_i g_i at fluid nodes
 // ---------------------------------------------------------------------------
-// Out of line: called from several places of the ghost-layer code, whose
-// inlined copies would multiply the stepping kernel's instruction footprint.
 template <int D, typename GT>
-__device__ __noinline__ float2 pop_moments(const DevParams &p, const float *__restrict__ f, const void *g, long long n)
+__device__ __forceinline__ float2 pop_moments(const DevParams &p, const float *__restrict__ f, const void *g, long long n)
 {
     constexpr int Q = Lat<D>::Q;
     float r = 0.f, ph = 0.f;
@@ -145,9 +143,8 @@ __global__ void __launch_bounds__(256) moments_batch_kernel(const BatchEntry *__
 // ghost layer (Sec. IV): average over fluid-facing axis directions; ghosts
 // with only diagonal fluid neighbours take the mean of those neighbours.
 // ---------------------------------------------------------------------------
-template <int D, class M>
-__device__ void ghost_value(const DevParams &p, const uint8_t *__restrict__ type, const M &mom, int x, int y, int z,
-                            float &gr_out, float &gp_out)
+template <int D, class A>
+__device__ void ghost_value(const DevParams &p, const A &acc, int x, int y, int z, float &gr_out, float &gp_out)
 {
     constexpr int Q = Lat<D>::Q;
     int c[3] = {x, y, z};
@@ -160,10 +157,10 @@ __device__ void ghost_value(const DevParams &p, const uint8_t *__restrict__ type
         for (int s = -1; s <= 1; s += 2) {
             int q[3] = {c[0], c[1], c[2]};
             q[a] += s;
-            long long m = node_of(p, q[0], q[1], q[2]);
-            if (type[m] & TLB_SOLID) continue;
+            float2 m1;
+            if (!acc.get(q[0], q[1], q[2], m1)) continue;
             float gr, gp;
-            ghost_axis<D>(p, type, mom, q[0], q[1], q[2], a, gr, gp);
+            ghost_axis<D>(p, acc, q[0], q[1], q[2], a, m1, gr, gp);
             sr += gr;
             sp += gp;
             ++cnt;
@@ -171,12 +168,10 @@ __device__ void ghost_value(const DevParams &p, const uint8_t *__restrict__ type
     if (cnt == 0) {
 #pragma unroll 1
         for (int i = 1; i < Q; ++i) {
-            const int qx = x + cc<D>(i, 0), qy = y + cc<D>(i, 1), qz = z + cc<D>(i, 2);
-            long long m = node_of(p, qx, qy, qz);
-            if (type[m] & TLB_SOLID) continue;
-            const float2 a = mom(qx, qy, qz, m);
-            sr += a.x;
-            sp += a.y;
+            float2 m;
+            if (!acc.get(x + cc<D>(i, 0), y + cc<D>(i, 1), z + cc<D>(i, 2), m)) continue;
+            sr += m.x;
+            sp += m.y;
             ++cnt;
         }
     }
@@ -189,7 +184,7 @@ __device__ void ghost_node(const DevParams &p, const uint8_t *__restrict__ type,
 {
     float gr, gp;
     const int x = (int)(n % p.nx), y = (int)((n / p.nx) % p.ny), z = (int)(n / ((long long)p.nx * p.ny));
-    ghost_value<D>(p, type, MomArrays{rho, phi}, x, y, z, gr, gp);
+    ghost_value<D>(p, NodesGlobal{p, type, rho, phi}, x, y, z, gr, gp);
     rho[n] = gr;
     phi[n] = gp;
 }
@@ -281,27 +276,44 @@ __device__ __forceinline__ int qcomp(int a, int b)
     return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
 }
 
-// Moments of a fluid node for the ghost layer when a tile sums its own
-// moments: from the tile + halo-2 region in shared memory when the node lies
-// there, else summed from the node's populations.  (ox, oy, oz) is the
+// Flag test and moments of a node outside the tile region: from the flag
+// array and the node's populations.  Out of line, so that the several call
+// sites of the ghost-layer code share one copy of the index arithmetic.
+template <int D, typename GT>
+__device__ __noinline__ bool node_far(const DevParams &p, const uint8_t *__restrict__ type, const float *__restrict__ f,
+                                      const void *g, int x, int y, int z, float2 &m)
+{
+    const long long n = node_of(p, x, y, z);
+    if (type[n] & TLB_SOLID) return false;
+    m = pop_moments<D, GT>(p, f, g, n);
+    return true;
+}
+
+// Node accessor of a tile that sums its own moments: node flags and moments
+// from the tile + halo-2 region in shared memory when the node lies there,
+// else from the flag array and the node's populations.  (ox, oy, oz) is the
 // region's first node; region slots at or beyond n + 2 along an axis are not
 // filled and are not read.
 template <int D, typename GT, int RX, int RY, int RZ>
-struct MomTile {
+struct NodesTile {
     const DevParams &p;
+    const uint8_t *type;
     const float *f;
     const void *g;
+    const uint8_t *srt;
     const float *srho, *sphi;
     int ox, oy, oz;
-    __device__ __forceinline__ float2 operator()(int x, int y, int z, long long n) const
+    __device__ __forceinline__ bool get(int x, int y, int z, float2 &m) const
     {
         const int lx = x - ox, ly = y - oy, lz = z - oz;
         if ((unsigned)lx < (unsigned)RX && (unsigned)ly < (unsigned)RY && (unsigned)lz < (unsigned)RZ &&
             x < p.nx + 2 && y < p.ny + 2 && z < p.nz + 2) {
             const int k = lx + RX * (ly + RY * lz);
-            return make_float2(srho[k], sphi[k]);
+            if (srt[k] & TLB_SOLID) return false;
+            m = make_float2(srho[k], sphi[k]);
+            return true;
         }
-        return pop_moments<D, GT>(p, f, g, n);
+        return node_far<D, GT>(p, type, f, g, x, y, z, m);
     }
 };
 
@@ -330,6 +342,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     __shared__ float sQ[NC][NS];
     __shared__ float smu[NS];
     __shared__ uint8_t stype[NS];
+    __shared__ uint8_t srt[FUSED ? NR : 1];   // FUSED: node flags of the tile + halo 2
     const int tid = threadIdx.x;
     constexpr int NT = TX * TY * TZ;
     extern __shared__ float stage[];          // ASYNC: f[Q][NT], then FP32 g[Q][NT]
@@ -428,8 +441,9 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         for (int s = 0; s < 2; ++s) {
             if (s == 1 && !has_h) break;
             float r = 0.f, ph = 0.f;
+            uint8_t t = TLB_SOLID;
             if (in[s]) {
-                const uint8_t t = __ldg(type + na[s]);
+                t = __ldg(type + na[s]);
                 ghost |= (t & TLB_GHOST) != 0;
                 if (!(t & TLB_SOLID)) {
                     // the summation order of the moments kernel
@@ -443,19 +457,21 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             }
             srho[kl[s]] = r;
             sphi[kl[s]] = ph;
+            srt[kl[s]] = t;
         }
         // Stage A2: the ghost layer of Sec. IV from the fluid moments
         if (__syncthreads_or(ghost)) {
-            const MomTile<D, GT, RX, RY, RZ> mom{p, f_in, g_in, srho, sphi, x0 - 2, y0 - 2, 0};
+            const NodesTile<D, GT, RX, RY, RZ> acc{p, type, f_in, g_in, srt, srho, sphi, x0 - 2, y0 - 2, 0};
             for (int k = tid; k < NR; k += blockDim.x) {
-                const int X = x0 - 2 + k % RX, Y = y0 - 2 + k / RX;
-                if (X >= p.nx + 2 || Y >= p.ny + 2) continue;
-                if (!(__ldg(type + node_near(p, X, Y, 0)) & TLB_GHOST)) continue;
+                if (!(srt[k] & TLB_GHOST)) continue;      // unfilled slots hold TLB_SOLID alone
                 float gr, gp;
-                ghost_value<D>(p, type, mom, X, Y, 0, gr, gp);
+                ghost_value<D>(p, acc, x0 - 2 + k % RX, y0 - 2 + k / RX, 0, gr, gp);
                 srho[k] = gr;
                 sphi[k] = gp;
             }
+            // the ghost code diverges within a warp: reconverge before the
+            // later stages, which would otherwise run once per split group
+            __syncwarp();
         }
     } else {
         // Stage A: rho, phi of the tile + halo 2, the ghost layer of Sec. IV
@@ -471,7 +487,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             long long n = node_near(p, X, Y, Z);
             if (__ldg(type + n) & TLB_GHOST) {
                 float gr, gp;
-                ghost_value<D>(p, type, MomArrays{rho, phi}, X, Y, Z, gr, gp);
+                ghost_value<D>(p, NodesGlobal{p, type, rho, phi}, X, Y, Z, gr, gp);
                 srho[k] = gr;
                 sphi[k] = gp;
             } else {
@@ -482,9 +498,11 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
     // node flags of the tile + halo 1
     for (int k = tid; k < NS; k += blockDim.x) {
-        const int X = x0 - 1 + k % SX, Y = y0 - 1 + (k / SX) % SY, Z = z0 - HZ1 + k / (SX * SY);
-        stype[k] = (X >= p.nx + 1 || Y >= p.ny + 1 || Z >= p.nz + 1) ? (uint8_t)TLB_SOLID
-                                                                      : __ldg(type + node_near(p, X, Y, Z));
+        const int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
+        const int X = x0 - 1 + lx, Y = y0 - 1 + ly, Z = z0 - HZ1 + lz;
+        if (X >= p.nx + 1 || Y >= p.ny + 1 || Z >= p.nz + 1) stype[k] = TLB_SOLID;
+        else if (FUSED) stype[k] = srt[(lx + 1) + RX * (ly + 1)];
+        else stype[k] = __ldg(type + node_near(p, X, Y, Z));
     }
     __syncthreads();
 
