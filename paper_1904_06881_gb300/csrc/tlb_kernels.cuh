@@ -289,31 +289,29 @@ __device__ __noinline__ bool node_far(const DevParams &p, const uint8_t *__restr
     return true;
 }
 
-// Node accessor of a tile that sums its own moments: node flags and moments
-// from the tile + halo-2 region in shared memory when the node lies there,
-// else from the flag array and the node's populations.  (ox, oy, oz) is the
-// region's first node; region slots at or beyond n + 2 along an axis are not
-// filled and are not read.
-template <int D, typename GT, int RX, int RY, int RZ>
-struct NodesTile {
+// Node accessor of the ghost pass of a D2Q9 tile that sums its own moments:
+// node flags and moments from a box in shared memory (the tile + halo 2 and a
+// margin that holds the samples of the ghost layer), else from the flag
+// array and the node's populations.  (ox, oy) is the box's first node.
+template <int D, typename GT, int BX, int BY>
+struct NodesBox {
     const DevParams &p;
     const uint8_t *type;
     const float *f;
     const void *g;
-    const uint8_t *srt;
-    const float *srho, *sphi;
-    int ox, oy, oz;
-    __device__ __forceinline__ bool get(int x, int y, int z, float2 &m) const
+    const uint8_t *bt;
+    const float *br, *bp;
+    int ox, oy;
+    __device__ __forceinline__ bool get(int x, int y, int, float2 &m) const
     {
-        const int lx = x - ox, ly = y - oy, lz = z - oz;
-        if ((unsigned)lx < (unsigned)RX && (unsigned)ly < (unsigned)RY && (unsigned)lz < (unsigned)RZ &&
-            x < p.nx + 2 && y < p.ny + 2 && z < p.nz + 2) {
-            const int k = lx + RX * (ly + RY * lz);
-            if (srt[k] & TLB_SOLID) return false;
-            m = make_float2(srho[k], sphi[k]);
+        const int lx = x - ox, ly = y - oy;
+        if ((unsigned)lx < (unsigned)BX && (unsigned)ly < (unsigned)BY) {
+            const int k = lx + BX * ly;
+            if (bt[k] & TLB_SOLID) return false;
+            m = make_float2(br[k], bp[k]);
             return true;
         }
-        return node_far<D, GT>(p, type, f, g, x, y, z, m);
+        return node_far<D, GT>(p, type, f, g, x, y, 0, m);
     }
 };
 
@@ -343,6 +341,13 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     __shared__ float smu[NS];
     __shared__ uint8_t stype[NS];
     __shared__ uint8_t srt[FUSED ? NR : 1];   // FUSED: node flags of the tile + halo 2
+    // FUSED tiles with ghost nodes: flags and moments of the tile + halo 2
+    // widened by EM nodes, the reach of the ghost layer (for theta in
+    // [20, 160] deg a ghost node's samples lie at most 3 nodes along the wall
+    // and 1 across from it; farther nodes are read from global memory)
+    constexpr int EM = 3, BX = RX + 2 * EM, BY = RY + 2 * EM, NB = FUSED ? BX * BY : 1;
+    __shared__ float brho[NB], bphi[NB];
+    __shared__ uint8_t btyp[NB];
     const int tid = threadIdx.x;
     constexpr int NT = TX * TY * TZ;
     extern __shared__ float stage[];          // ASYNC: f[Q][NT], then FP32 g[Q][NT]
@@ -461,7 +466,59 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         }
         // Stage A2: the ghost layer of Sec. IV from the fluid moments
         if (__syncthreads_or(ghost)) {
-            const NodesTile<D, GT, RX, RY, RZ> acc{p, type, f_in, g_in, srt, srho, sphi, x0 - 2, y0 - 2, 0};
+            // the box: region slots copied (where filled) ...
+            for (int k = tid; k < NR; k += blockDim.x) {
+                const int lx = k % RX, ly = k / RX, kb = (lx + EM) + BX * (ly + EM);
+                const int X = x0 - 2 + lx, Y = y0 - 2 + ly;
+                if (X < p.nx + 2 && Y < p.ny + 2) {
+                    btyp[kb] = srt[k];
+                    brho[kb] = srho[k];
+                    bphi[kb] = sphi[k];
+                } else {                      // lattices narrower than a tile
+                    const long long n = node_of(p, X, Y, 0);
+                    const uint8_t t = __ldg(type + n);
+                    const float2 m = pop_moments<D, GT>(p, f_in, g_in, n);
+                    btyp[kb] = t;
+                    brho[kb] = (t & TLB_SOLID) ? 0.f : m.x;
+                    bphi[kb] = (t & TLB_SOLID) ? 0.f : m.y;
+                }
+            }
+            // ... and the margin summed from the populations: at most two
+            // nodes per thread, all loads issued before the sums.  Margin
+            // index h: rows above, rows below, then the columns either side.
+            constexpr int NM = BX * BY - RX * RY;
+            static_assert(NM <= 2 * NT, "margin of two nodes per thread");
+            int kb[2];
+            long long nm[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int h = (tid + NT * j < NM) ? tid + NT * j : 0;
+                int bx, by;
+                if (h < EM * BX) { bx = h % BX; by = h / BX; }
+                else if (h < 2 * EM * BX) { bx = (h - EM * BX) % BX; by = BY - EM + (h - EM * BX) / BX; }
+                else {
+                    const int c = (h - 2 * EM * BX) % (2 * EM);
+                    bx = c < EM ? c : RX + c;
+                    by = EM + (h - 2 * EM * BX) / (2 * EM);
+                }
+                kb[j] = bx + BX * by;
+                nm[j] = node_of(p, x0 - 2 - EM + bx, y0 - 2 - EM + by, 0);
+            }
+            const uint8_t t0 = __ldg(type + nm[0]), t1 = __ldg(type + nm[1]);
+            const float2 m0 = pop_moments<D, GT>(p, f_in, g_in, nm[0]);
+            const float2 m1 = pop_moments<D, GT>(p, f_in, g_in, nm[1]);
+            if (tid < NM) {
+                btyp[kb[0]] = t0;
+                brho[kb[0]] = (t0 & TLB_SOLID) ? 0.f : m0.x;
+                bphi[kb[0]] = (t0 & TLB_SOLID) ? 0.f : m0.y;
+            }
+            if (tid + NT < NM) {
+                btyp[kb[1]] = t1;
+                brho[kb[1]] = (t1 & TLB_SOLID) ? 0.f : m1.x;
+                bphi[kb[1]] = (t1 & TLB_SOLID) ? 0.f : m1.y;
+            }
+            __syncthreads();
+            const NodesBox<D, GT, BX, BY> acc{p, type, f_in, g_in, btyp, brho, bphi, x0 - 2 - EM, y0 - 2 - EM};
             for (int k = tid; k < NR; k += blockDim.x) {
                 if (!(srt[k] & TLB_GHOST)) continue;      // unfilled slots hold TLB_SOLID alone
                 float gr, gp;
@@ -469,9 +526,6 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                 srho[k] = gr;
                 sphi[k] = gp;
             }
-            // the ghost code diverges within a warp: reconverge before the
-            // later stages, which would otherwise run once per split group
-            __syncwarp();
         }
     } else {
         // Stage A: rho, phi of the tile + halo 2, the ghost layer of Sec. IV
