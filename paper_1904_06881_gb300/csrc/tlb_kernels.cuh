@@ -871,8 +871,12 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_kernel(DevParams p, 
 // The stepping kernel of every lattice, alone or batched: one CTA per entry of
 // a tile table (lattice index, tile origin).  A lattice advanced alone is a
 // batch of one, so its results are bit-identical to the same lattice in a mix.
-template <int D, typename GT>
-__global__ void __launch_bounds__(256, D == 2 ? 3 : 2) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
+// MINB: resident CTAs per SM the registers are budgeted for.  D2Q9 comes in
+// two builds with the same code (the register allocation alone differs):
+// 3 CTAs/SM (80 registers, fewer spills) for launches that fit in one wave,
+// 4 CTAs/SM (64 registers, more warps to hide latency) for larger ones.
+template <int D, typename GT, int MINB>
+__global__ void __launch_bounds__(256, MINB) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
 {
     __shared__ BatchEntry se;
     pdl_trigger();
@@ -1099,12 +1103,27 @@ template <int D, typename GT>
 static void launch_step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, cudaStream_t st)
 {
     constexpr int bytes = stage_bytes<D, GT>();
-    static bool attr = false;   // the dynamic shared-memory opt-in, once per process
-    if (!attr) {
-        cudaFuncSetAttribute(step_batch_kernel<D, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        attr = true;
+    constexpr int nt = Tile<D>::X * Tile<D>::Y * Tile<D>::Z;
+    static bool attr = false;   // the dynamic shared-memory opt-ins, once per process
+    static int nsm = 0;         // SMs of the device (D2Q9: the one-wave bound)
+    if constexpr (D == 2) {
+        if (!attr) {
+            cudaFuncSetAttribute(step_batch_kernel<D, GT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            cudaFuncSetAttribute(step_batch_kernel<D, GT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            attr = true;
+        }
+        if (ntiles > 3 * nsm) launch_pdl(step_batch_kernel<D, GT, 4>, ntiles, nt, (size_t)bytes, st, entries, tiles);
+        else launch_pdl(step_batch_kernel<D, GT, 3>, ntiles, nt, (size_t)bytes, st, entries, tiles);
+    } else {
+        if (!attr) {
+            cudaFuncSetAttribute(step_batch_kernel<D, GT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            attr = true;
+        }
+        launch_pdl(step_batch_kernel<D, GT, 2>, ntiles, nt, (size_t)bytes, st, entries, tiles);
     }
-    launch_pdl(step_batch_kernel<D, GT>, ntiles, Tile<D>::X * Tile<D>::Y * Tile<D>::Z, (size_t)bytes, st, entries, tiles);
 }
 
 template <int D>

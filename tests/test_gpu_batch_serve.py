@@ -69,3 +69,20 @@ def test_server_alone_vs_mix():
         a = tlb.lattice_from_workload(wl)
         a.step(n)
         assert _same(a.fields(), r)
+
+
+def test_one_wave_and_large_launches_agree():
+    """A D2Q9 launch with more tiles than fit on the GPU at 3 CTAs per SM runs
+    the 64-register build of the step kernel, a smaller one the 80-register
+    build of the same code.  A lattice alone (small launch) and in a mix with a
+    512 x 512 lattice (large launch) gives bit-identical fields."""
+    from paper_1904_06881_gb300 import tlb
+
+    specs = [(64, 45.0, W.WET_GEOM_INTERP), (96, 90.0, W.WET_FORCE), (64, 120.0, W.WET_GEOM_EXTRAP)]
+    alone = [_drop(L, th, wet)[1] for L, th, wet in specs]
+    mix = [_drop(L, th, wet)[1] for L, th, wet in specs] + [_drop(512, 60.0, W.WET_GEOM_INTERP)[1]]
+    for a in alone:
+        a.step(200)
+    tlb.tlb_step_batch([m.h for m in mix], 200)
+    for a, m in zip(alone, mix):
+        assert _same(a.fields(), m.fields())
