@@ -340,7 +340,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     __shared__ float sQ[NC][NS];
     __shared__ float smu[NS];
     __shared__ uint8_t stype[NS];
-    __shared__ uint8_t srt[FUSED ? NR : 1];   // FUSED: node flags of the tile + halo 2
+    __shared__ uint8_t srt[NR];               // node flags of the tile + halo 2
     // FUSED tiles with ghost nodes: flags and moments of the tile + halo 2
     // widened by EM nodes, the reach of the ghost layer (for theta in
     // [20, 160] deg a ghost node's samples lie at most 3 nodes along the wall
@@ -528,35 +528,53 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             }
         }
     } else {
-        // Stage A: rho, phi of the tile + halo 2, the ghost layer of Sec. IV
-        // filled here from the fluid moments (the moments pass leaves ghost
-        // nodes alone)
-        for (int k = tid; k < NR; k += blockDim.x) {
+        // Stage A: rho, phi and flags of the tile + halo 2, all of a thread's
+        // slots loaded in one round (loads issued before use); then the ghost
+        // layer of Sec. IV from the fluid moments (the moments pass leaves
+        // ghost nodes alone)
+        constexpr int PER = (NR + NT - 1) / NT;
+        float lr[PER], lp[PER];
+        uint8_t lt[PER];
+        bool ghost = false;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int k = tid + NT * j;
             const int X = x0 - 2 + k % RX, Y = y0 - 2 + (k / RX) % RY, Z = z0 - HZ2 + k / (RX * RY);
-            if (X >= p.nx + 2 || Y >= p.ny + 2 || Z >= p.nz + 2) {
-                srho[k] = 0.f;
-                sphi[k] = 0.f;
-                continue;
-            }
-            long long n = node_near(p, X, Y, Z);
-            if (__ldg(type + n) & TLB_GHOST) {
+            const bool in = k < NR && X < p.nx + 2 && Y < p.ny + 2 && Z < p.nz + 2;
+            const long long n = in ? node_near(p, X, Y, Z) : 0;
+            lt[j] = in ? __ldg(type + n) : (uint8_t)TLB_SOLID;
+            lr[j] = in ? __ldg(rho + n) : 0.f;
+            lp[j] = in ? __ldg(phi + n) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int k = tid + NT * j;
+            if (k >= NR) break;
+            srt[k] = lt[j];
+            srho[k] = lr[j];
+            sphi[k] = lp[j];
+            ghost |= (lt[j] & TLB_GHOST) != 0;
+        }
+        if (ghost) {
+            const NodesGlobal acc{p, type, rho, phi};
+#pragma unroll 1
+            for (int k = tid; k < NR; k += NT) {
+                if (!(srt[k] & TLB_GHOST)) continue;      // unfilled slots hold TLB_SOLID alone
                 float gr, gp;
-                ghost_value<D>(p, NodesGlobal{p, type, rho, phi}, X, Y, Z, gr, gp);
+                ghost_value<D>(p, acc, x0 - 2 + k % RX, y0 - 2 + (k / RX) % RY, z0 - HZ2 + k / (RX * RY), gr, gp);
                 srho[k] = gr;
                 sphi[k] = gp;
-            } else {
-                srho[k] = __ldg(rho + n);
-                sphi[k] = __ldg(phi + n);
             }
         }
+        __syncthreads();
     }
-    // node flags of the tile + halo 1
+    // node flags of the tile + halo 1, from those of the region
     for (int k = tid; k < NS; k += blockDim.x) {
         const int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
         const int X = x0 - 1 + lx, Y = y0 - 1 + ly, Z = z0 - HZ1 + lz;
-        if (X >= p.nx + 1 || Y >= p.ny + 1 || Z >= p.nz + 1) stype[k] = TLB_SOLID;
-        else if (FUSED) stype[k] = srt[(lx + 1) + RX * (ly + 1)];
-        else stype[k] = __ldg(type + node_near(p, X, Y, Z));
+        stype[k] = (X >= p.nx + 1 || Y >= p.ny + 1 || Z >= p.nz + 1)
+                       ? (uint8_t)TLB_SOLID
+                       : srt[(lx + 1) + RX * ((ly + 1) + RY * (lz + (D == 3 ? 1 : 0)))];
     }
     __syncthreads();
 
