@@ -162,32 +162,47 @@ __device__ __forceinline__ float phi_ent(float y, float l)
 //   h'(alpha) = sum_i f'_i x_i [ ln(1 + alpha x_i) - ln(1 + x_i) ],
 //   h''(alpha) = sum_i f'_i x_i^2 / (1 + alpha x_i),
 // which involves no difference of O(1) entropies.  Expanding h/alpha in x
-// with the moments a_k = sum_i f'_i x_i^k and solving alpha = 2 + e1 + e2 + e3
-// order by order gives
-//   e1 = a3 / (3 a2),  e2 = 2 (2 a3^2 - 3 a2 a4) / (9 a2^2),
-//   e3 = (297 a2^2 a5 - 420 a2 a3 a4 + 170 a3^3) / (270 a2^3),
-// used as is up to max|x| = 0.03 (its effect on f stays below 1e-8 there) and as
-// the start of Halley's method (third order, from h, h', h''), bracketed by
-// [1, alpha_max), above it (nodes at the interface).
+// with the moments a_k = sum_i f'_i x_i^k (a_1 = 0), b_k = a_k / a_2, and
+// solving alpha = 2 + e1 + ... + e5 order by order gives
+//   e1 = b3 / 3,  e2 = 2 (2 b3^2 - 3 b4) / 9,
+//   e3 = (297 b5 - 420 b3 b4 + 170 b3^3) / 270,
+//   e4 = (1026 b3 b5 + 540 b4^2 - 702 b6 - 1305 b3^2 b4 + 380 b3^4) / 405,
+//   e5 = (15390 b7 - 23184 b3 b6 - 24570 b4 b5 + 30114 b3^2 b5 + 31080 b3 b4^2
+//         - 36295 b3^3 b4 + 8260 b3^5) / 5670,
+// used as is up to max|x| = 0.07 (against the exact root of random D2Q9 and
+// D3Q27 states its truncation error is below 5e-8 there, and its FP32 value
+// within 2.5e-7, one or two units in the last place of alpha; either moves f
+// by less than 2e-8 of itself) and as the start of Halley's method (third
+// order, from h, h', h''), bracketed by [1, alpha_max), above it (nodes at the
+// interface).
 template <int Q>
 __device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&x)[Q])
 {
-    float a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
+    float a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f, a7 = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float x2 = x[i] * x[i];
-        float fx2 = fp[i] * x2;
+        const float x2 = x[i] * x[i];
+        const float fx2 = fp[i] * x2, fx4 = fx2 * x2;
         a2 += fx2;
         a3 += fx2 * x[i];
-        a4 += fx2 * x2;
-        a5 += fx2 * x2 * x[i];
+        a4 += fx4;
+        a5 += fx4 * x[i];
+        a6 += fx4 * x2;
+        a7 += fx4 * x2 * x[i];
     }
     if (!(a2 > 0.f)) return 2.0f;
-    float r = 1.0f / a2, t = a3 * r;
-    float e1 = t * (1.0f / 3.0f);
-    float e2 = (2.0f / 9.0f) * (2.0f * t * t - 3.0f * a4 * r);
-    float e3 = (297.0f * a5 * r - 420.0f * t * a4 * r + 170.0f * t * t * t) * (1.0f / 270.0f);
-    return 2.0f + e1 + e2 + e3;
+    const float r = 1.0f / a2;
+    const float b3 = a3 * r, b4 = a4 * r, b5 = a5 * r, b6 = a6 * r, b7 = a7 * r;
+    const float b33 = b3 * b3;
+    const float e1 = b3 * (1.0f / 3.0f);
+    const float e2 = (2.0f / 9.0f) * (2.0f * b33 - 3.0f * b4);
+    const float e3 = (297.0f * b5 - 420.0f * b3 * b4 + 170.0f * b33 * b3) * (1.0f / 270.0f);
+    const float e4 = (1026.0f * b3 * b5 + 540.0f * b4 * b4 - 702.0f * b6 - 1305.0f * b33 * b4 + 380.0f * b33 * b33) *
+                     (1.0f / 405.0f);
+    const float e5 = (15390.0f * b7 - 23184.0f * b3 * b6 - 24570.0f * b4 * b5 + 30114.0f * b33 * b5 +
+                      31080.0f * b3 * b4 * b4 - 36295.0f * b33 * b3 * b4 + 8260.0f * b33 * b33 * b3) *
+                     (1.0f / 5670.0f);
+    return 2.0f + e1 + e2 + e3 + e4 + e5;
 }
 
 // Root of h in (1, alpha_max) from the start al.  h(1) < 0 always; when h is

@@ -823,7 +823,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         atomicOr(status, 1u);
     } else if (xmax >= 1e-5f) {
         al = alpha_series<Q>(fp, dl);
-        if (xmax > 0.03f) {
+        if (xmax > 0.07f) {
             const float amax = xneg > 0.f ? 1.0f / xneg : 3.0e38f;
             al = alpha_newton<Q>(fp, dl, amax, al);
         }
