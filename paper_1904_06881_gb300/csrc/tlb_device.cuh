@@ -292,36 +292,36 @@ template <int D, class A>
 __device__ void ghost_axis(const DevParams &p, const A &acc, int yx, int yy, int yz, int axis, float2 m1, float &gr,
                            float &gp)
 {
+    // Coordinates are kept in scalars (an array indexed by the run-time axis
+    // would live in local memory): the in-plane axes are t0 = first axis other
+    // than `axis`, t1 = the second (3D), as unit offsets (ux, uy, uz), (vx, vy, vz).
     const float r1 = m1.x, p1 = m1.y;
     if (p.wetting == TLB_WET_FORCE) { gr = r1; gp = p1; return; }
-    constexpr int nt = D - 1;                 // in-plane axes
-    int T[2];
-    T[0] = axis == 0 ? 1 : 0;
-    T[1] = axis == 2 ? 1 : 2;
-    float dr[2] = {0.f, 0.f}, dp[2] = {0.f, 0.f};
-    int yc[3] = {yx, yy, yz};
-#pragma unroll
-    for (int k = 0; k < nt; ++k) {
-        int cp[3] = {yc[0], yc[1], yc[2]}, cm[3] = {yc[0], yc[1], yc[2]};
-        cp[T[k]] += 1;
-        cm[T[k]] -= 1;
+    const int t0 = axis == 0 ? 1 : 0, t1 = axis == 2 ? 1 : 2;
+    const int ux = t0 == 0, uy = t0 == 1, uz = 0;
+    const int vx = 0, vy = (D == 3 && t1 == 1), vz = (D == 3 && t1 == 2);
+    // in-plane central (one-sided next to solid) differences of rho, phi
+    auto diff = [&](int ox, int oy, int oz, float &dr, float &dp) {
         float2 a, b;
-        const bool fp_ = acc.get(cp[0], cp[1], cp[2], a), fm = acc.get(cm[0], cm[1], cm[2], b);
+        const bool fp_ = acc.get(yx + ox, yy + oy, yz + oz, a), fm = acc.get(yx - ox, yy - oy, yz - oz, b);
+        dr = 0.f;
+        dp = 0.f;
         if (fp_ && fm) {
-            dr[k] = 0.5f * (a.x - b.x);
-            dp[k] = 0.5f * (a.y - b.y);
+            dr = 0.5f * (a.x - b.x);
+            dp = 0.5f * (a.y - b.y);
         } else if (fp_) {
-            dr[k] = a.x - r1;
-            dp[k] = a.y - p1;
+            dr = a.x - r1;
+            dp = a.y - p1;
         } else if (fm) {
-            dr[k] = r1 - b.x;
-            dp[k] = p1 - b.y;
+            dr = r1 - b.x;
+            dp = p1 - b.y;
         }
-    }
-    float nr = 0.f, npp = 0.f, dot = 0.f;
-    for (int k = 0; k < nt; ++k) { nr += dr[k] * dr[k]; npp += dp[k] * dp[k]; dot += dr[k] * dp[k]; }
-    nr = sqrtf(nr);
-    npp = sqrtf(npp);
+    };
+    float dr0, dp0, dr1 = 0.f, dp1 = 0.f;
+    diff(ux, uy, uz, dr0, dp0);
+    if (D == 3) diff(vx, vy, vz, dr1, dp1);
+    const float nr = sqrtf(dr0 * dr0 + dr1 * dr1), npp = sqrtf(dp0 * dp0 + dp1 * dp1);
+    const float dot = dr0 * dp0 + dr1 * dp1;
     // interface identification (Sec. IV.B): 0 = 1-2, 1 = 1-3, 2 = 2-3
     int pair;
     if (nr < 0.01f * (p.rho_l - p.rho_g) * p.inv_chi * npp) pair = 2;
@@ -329,26 +329,23 @@ __device__ void ghost_axis(const DevParams &p, const A &acc, int yx, int yy, int
     else if (r1 > 0.5f * p.rho_l && p1 > 0.95f * p.chi) pair = 0;
     else if (dot < 0.f) pair = 1;
     else pair = 0;
-    const float *dc = (pair == 2) ? dp : dr;
-    float nc = (pair == 2) ? npp : nr;
-    float cot = p.cot[pair];
+    const float dc0 = pair == 2 ? dp0 : dr0, dc1 = pair == 2 ? dp1 : dr1;
+    const float nc = pair == 2 ? npp : nr;
+    const float cot = pair == 0 ? p.cot[0] : (pair == 1 ? p.cot[1] : p.cot[2]);
     if (!(nc > 1e-12f)) { gr = r1; gp = p1; return; }
-    float tx = dc[0] / nc, ty = (nt > 1) ? dc[1] / nc : 0.f;
+    const float tx = dc0 / nc, ty = D == 3 ? dc1 / nc : 0.f;
     if (p.wetting == TLB_WET_GEOM_EXTRAP) {
         // Eqs. geomamgle, geomding; the second field follows the same interface
-        float sr = dr[0] * tx + (nt > 1 ? dr[1] * ty : 0.f);
-        float sp = dp[0] * tx + (nt > 1 ? dp[1] * ty : 0.f);
+        const float sr = dr0 * tx + (D == 3 ? dr1 * ty : 0.f);
+        const float sp = dp0 * tx + (D == 3 ? dp1 * ty : 0.f);
         gr = r1 + cot * sr;
         gp = p1 + cot * sp;
         return;
     }
     // geometric interpolation: sample at cot(theta) t_hat in the first fluid layer
     auto samp = [&](int k1, int k2, float &vr, float &vp) {
-        int q[3] = {yc[0], yc[1], yc[2]};
-        q[T[0]] += k1;
-        if (nt > 1) q[T[1]] += k2;
         float2 a;
-        if (acc.get(q[0], q[1], q[2], a)) {
+        if (acc.get(yx + k1 * ux + k2 * vx, yy + k1 * uy + k2 * vy, yz + k1 * uz + k2 * vz, a)) {
             vr = a.x;
             vp = a.y;
         } else {
@@ -356,46 +353,44 @@ __device__ void ghost_axis(const DevParams &p, const A &acc, int yx, int yy, int
             vp = p1;
         }
     };
-    if (nt == 1) {
-        float l = cot * tx;
-        int l0 = (int)floorf(l), l1 = l0 + 1;
+    if (D == 2) {
+        const float l = cot * tx;
+        const int l0 = (int)floorf(l), l1 = l0 + 1;
         float v0r, v0p, v1r, v1p;
         samp(l0, 0, v0r, v0p);
         samp(l1, 0, v1r, v1p);
-        float t = l - (float)l0;                 // linear interpolation on [l0, l1] (Eq. interp2D)
+        const float t = l - (float)l0;           // linear interpolation on [l0, l1] (Eq. interp2D)
         gr = v0r + t * (v1r - v0r);
         gp = v0p + t * (v1p - v0p);
         return;
     }
-    float lx = cot * tx, ly = cot * ty;
+    const float lx = cot * tx, ly = cot * ty;
     if (sqrtf(lx * lx + ly * ly) < 1e-12f) { gr = r1; gp = p1; return; }
-    int X0 = (int)floorf(lx), Y0 = (int)floorf(ly);
-    // of the four corners of the unit cell around (lx, ly), drop the one nearest
-    // to the origin (first of (0,0),(1,0),(0,1),(1,1) on ties) (Eq. interp3D)
-    int drop = 0;
-    int best = 1 << 30;
-    for (int k = 0; k < 4; ++k) {
-        int cx = X0 + (k & 1), cy = Y0 + (k >> 1);
-        int d2 = cx * cx + cy * cy;
+    const int X0 = (int)floorf(lx), Y0 = (int)floorf(ly);
+    // of the four corners k = 0..3 at (X0 + (k & 1), Y0 + (k >> 1)) of the unit
+    // cell around (lx, ly), drop the one nearest to the origin (first of
+    // (0,0),(1,0),(0,1),(1,1) on ties) (Eq. interp3D); keep the other three in order
+    int drop = 0, best = X0 * X0 + Y0 * Y0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        const int cx = X0 + (k & 1), cy = Y0 + (k >> 1);
+        const int d2 = cx * cx + cy * cy;
         if (d2 < best) { best = d2; drop = k; }
     }
-    float xs[3], ys[3], vr[3], vp[3];
-    int m = 0;
-    for (int k = 0; k < 4; ++k) {
-        if (k == drop) continue;
-        int cx = X0 + (k & 1), cy = Y0 + (k >> 1);
-        xs[m] = (float)cx;
-        ys[m] = (float)cy;
-        samp(cx, cy, vr[m], vp[m]);
-        ++m;
-    }
+    const int ka = drop == 0 ? 1 : 0, kb = drop <= 1 ? 2 : 1, kc = drop <= 2 ? 3 : 2;
+    const int ax = X0 + (ka & 1), ay = Y0 + (ka >> 1), bx = X0 + (kb & 1), by = Y0 + (kb >> 1);
+    const int cxx = X0 + (kc & 1), cyy = Y0 + (kc >> 1);
+    float v0r, v0p, v1r, v1p, v2r, v2p;
+    samp(ax, ay, v0r, v0p);
+    samp(bx, by, v1r, v1p);
+    samp(cxx, cyy, v2r, v2p);
     // barycentric coordinates of (lx, ly) in the triangle
-    float e1x = xs[1] - xs[0], e1y = ys[1] - ys[0], e2x = xs[2] - xs[0], e2y = ys[2] - ys[0];
-    float det = e1x * e2y - e2x * e1y;
-    float px = lx - xs[0], py = ly - ys[0];
-    float b1 = (px * e2y - e2x * py) / det, b2 = (e1x * py - px * e1y) / det;
-    gr = vr[0] + b1 * (vr[1] - vr[0]) + b2 * (vr[2] - vr[0]);
-    gp = vp[0] + b1 * (vp[1] - vp[0]) + b2 * (vp[2] - vp[0]);
+    const float e1x = (float)(bx - ax), e1y = (float)(by - ay), e2x = (float)(cxx - ax), e2y = (float)(cyy - ay);
+    const float det = e1x * e2y - e2x * e1y;
+    const float px = lx - (float)ax, py = ly - (float)ay;
+    const float b1 = (px * e2y - e2x * py) / det, b2 = (e1x * py - px * e1y) / det;
+    gr = v0r + b1 * (v1r - v0r) + b2 * (v2r - v0r);
+    gp = v0p + b1 * (v1p - v0p) + b2 * (v2p - v0p);
 }
 
 }  // namespace tlb

@@ -147,24 +147,22 @@ template <int D, class A>
 __device__ void ghost_value(const DevParams &p, const A &acc, int x, int y, int z, float &gr_out, float &gp_out)
 {
     constexpr int Q = Lat<D>::Q;
-    int c[3] = {x, y, z};
     float sr = 0.f, sp = 0.f;
     int cnt = 0;
-    // one copy of the (large) axis code, not one per direction
+    // one copy of the (large) axis code, not one per direction; scalar
+    // coordinates (no array indexed by the run-time axis)
 #pragma unroll 1
-    for (int a = 0; a < D; ++a)
-#pragma unroll 1
-        for (int s = -1; s <= 1; s += 2) {
-            int q[3] = {c[0], c[1], c[2]};
-            q[a] += s;
-            float2 m1;
-            if (!acc.get(q[0], q[1], q[2], m1)) continue;
-            float gr, gp;
-            ghost_axis<D>(p, acc, q[0], q[1], q[2], a, m1, gr, gp);
-            sr += gr;
-            sp += gp;
-            ++cnt;
-        }
+    for (int d = 0; d < 2 * D; ++d) {
+        const int a = d >> 1, s = (d & 1) ? 1 : -1;
+        const int qx = x + (a == 0 ? s : 0), qy = y + (a == 1 ? s : 0), qz = z + (a == 2 ? s : 0);
+        float2 m1;
+        if (!acc.get(qx, qy, qz, m1)) continue;
+        float gr, gp;
+        ghost_axis<D>(p, acc, qx, qy, qz, a, m1, gr, gp);
+        sr += gr;
+        sp += gp;
+        ++cnt;
+    }
     if (cnt == 0) {
 #pragma unroll 1
         for (int i = 1; i < Q; ++i) {
@@ -348,6 +346,9 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     constexpr int EM = 3, BX = RX + 2 * EM, BY = RY + 2 * EM, NB = FUSED ? BX * BY : 1;
     __shared__ float brho[NB], bphi[NB];
     __shared__ uint8_t btyp[NB];
+    // FUSED: the region's ghost slots, one per thread in the ghost pass
+    __shared__ short glist[FUSED ? NR : 1];
+    __shared__ int nghost;
     const int tid = threadIdx.x;
     constexpr int NT = TX * TY * TZ;
     extern __shared__ float stage[];          // ASYNC: f[Q][NT], then FP32 g[Q][NT]
@@ -442,6 +443,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             }
         }
         bool ghost = false;
+        if (tid == 0) nghost = 0;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (s == 1 && !has_h) break;
@@ -466,6 +468,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         }
         // Stage A2: the ghost layer of Sec. IV from the fluid moments
         if (__syncthreads_or(ghost)) {
+            // list the ghost slots (in any order: each ghost value depends on
+            // the box alone), so that no thread takes more than one of them
+            for (int k = tid; k < NR; k += blockDim.x)
+                if (srt[k] & TLB_GHOST) glist[atomicAdd(&nghost, 1)] = (short)k;
             // the box: region slots copied (where filled) ...
             for (int k = tid; k < NR; k += blockDim.x) {
                 const int lx = k % RX, ly = k / RX, kb = (lx + EM) + BX * (ly + EM);
@@ -519,8 +525,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             }
             __syncthreads();
             const NodesBox<D, GT, BX, BY> acc{p, type, f_in, g_in, btyp, brho, bphi, x0 - 2 - EM, y0 - 2 - EM};
-            for (int k = tid; k < NR; k += blockDim.x) {
-                if (!(srt[k] & TLB_GHOST)) continue;      // unfilled slots hold TLB_SOLID alone
+            for (int j = tid; j < nghost; j += blockDim.x) {
+                const int k = glist[j];
                 float gr, gp;
                 ghost_value<D>(p, acc, x0 - 2 + k % RX, y0 - 2 + k / RX, 0, gr, gp);
                 srho[k] = gr;
