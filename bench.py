@@ -145,8 +145,9 @@ def algorithmic_bytes(Q, N):
 
 
 def measure(lat, stream, steps, warmup, flush=None, kernel_steps=None):
-    """Per-step time of whole steps (tlb_step: one CUDA graph of the step's
-    launches) and the average duration of the fused step kernel alone (launched
+    """Per-step time of whole steps (tlb_step: one launch for D2Q9, a CUDA
+    graph of the two launches for D3Q27) and the average duration of the fused
+    step kernel alone (launched
     through tlb_step_phase; phase 0, the D3Q27 moments pass, is outside the
     kernel's events), both with CUDA events on the lattice's stream.
     With `flush`, a buffer larger than L2 is written before every timed step."""

@@ -391,7 +391,7 @@ struct tlb_ctx {
     BatchEntry *self_entries = nullptr;
     int4 *self_tiles = nullptr;
     int nself_tiles = 0;
-    // one CUDA graph per buffer parity holding the three launches of a step
+    // one CUDA graph per buffer parity holding the launches of a step (D3Q27)
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaStream_t cap_stream = nullptr;
 };
@@ -802,9 +802,14 @@ extern "C" int tlb_step(tlb_ctx *c, int nsteps)
     if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
     const int per = launches_per_step(c->D);
     for (int k = 0; k < nsteps; ++k) {
-        int rc = capture_step(c);
-        if (rc) return rc;
-        CUDA_TRY(cudaGraphLaunch(c->gexec[c->s.cur], c->stream));
+        if (per == 1) {
+            // a single launch: direct (a one-node graph costs more to launch)
+            issue_step_on(c, c->stream);
+        } else {
+            int rc = capture_step(c);
+            if (rc) return rc;
+            CUDA_TRY(cudaGraphLaunch(c->gexec[c->s.cur], c->stream));
+        }
         c->s.cur ^= 1;
         c->steps += 1;
         c->launches += per;
