@@ -352,31 +352,6 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     const int tid = threadIdx.x;
     constexpr int NT = TX * TY * TZ;
     extern __shared__ float stage[];          // ASYNC: f[Q][NT], then FP32 g[Q][NT]
-    if (ASYNC) {
-        const int ax = x0 + tid % TX, ay = y0 + (tid / TX) % TY, az = z0 + tid / (TX * TY);
-        if (ax < p.nx && ay < p.ny && az < p.nz) {
-            const long long an = (long long)ax + (long long)p.nx * ((long long)ay + (long long)p.ny * az);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) cp_async4(&stage[i * NT + tid], f_in + (long long)i * p.N + an);
-            if (sizeof(GT) == 4) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    cp_async4(&stage[(Q + i) * NT + tid], (const float *)g_in + (long long)i * p.N + an);
-            } else {
-                cp_async4(&stage[Q * NT + tid], (const float *)g_in + an);
-                // the FP16 moving populations of two x-neighbours share a 4-byte
-                // word (nx even): the even thread of each pair copies it
-                if ((p.nx & 1) == 0 && (tid & 1) == 0) {
-                    const char *h = (const char *)g_in + 4 * p.N;
-                    __half *s16 = reinterpret_cast<__half *>(&stage[(Q + 1) * NT]);
-#pragma unroll
-                    for (int i = 1; i < Q; ++i)
-                        cp_async4(&s16[(i - 1) * NT + tid], h + 2 * ((long long)(i - 1) * p.N + an));
-                }
-            }
-        }
-        cp_async_commit();
-    }
 
     // Region slots are filled for coordinates below n + 2 (n + 1 for the flags)
     // along each axis: the tile's nodes use no farther neighbours, and
@@ -551,6 +526,33 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             lt[j] = in ? __ldg(type + n) : (uint8_t)TLB_SOLID;
             lr[j] = in ? __ldg(rho + n) : 0.f;
             lp[j] = in ? __ldg(phi + n) : 0.f;
+        }
+        // the node's own populations for stage C, requested after the loads stage A
+        // waits on (they would queue ahead of them otherwise)
+        if (ASYNC) {
+            const int ax = x0 + tid % TX, ay = y0 + (tid / TX) % TY, az = z0 + tid / (TX * TY);
+            if (ax < p.nx && ay < p.ny && az < p.nz) {
+                const long long an = (long long)ax + (long long)p.nx * ((long long)ay + (long long)p.ny * az);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) cp_async4(&stage[i * NT + tid], f_in + (long long)i * p.N + an);
+                if (sizeof(GT) == 4) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i)
+                        cp_async4(&stage[(Q + i) * NT + tid], (const float *)g_in + (long long)i * p.N + an);
+                } else {
+                    cp_async4(&stage[Q * NT + tid], (const float *)g_in + an);
+                    // the FP16 moving populations of two x-neighbours share a 4-byte
+                    // word (nx even): the even thread of each pair copies it
+                    if ((p.nx & 1) == 0 && (tid & 1) == 0) {
+                        const char *h = (const char *)g_in + 4 * p.N;
+                        __half *s16 = reinterpret_cast<__half *>(&stage[(Q + 1) * NT]);
+#pragma unroll
+                        for (int i = 1; i < Q; ++i)
+                            cp_async4(&s16[(i - 1) * NT + tid], h + 2 * ((long long)(i - 1) * p.N + an));
+                    }
+                }
+            }
+            cp_async_commit();
         }
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
