@@ -335,7 +335,18 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     constexpr int HZ2 = (D == 3) ? 2 : 0, HZ1 = (D == 3) ? 1 : 0;
     constexpr int NC = NQC<D>();
     __shared__ float srho[NR], sphi[NR];
-    __shared__ float sQ[NC][NS];
+    // Q = rho c_s^2 I - P of the tile + halo 1: D2Q9 one array per component;
+    // D3Q27 per node as {xx, yy, zz, xy} and {xz, yz}, so that the force
+    // stencil reads a neighbour's tensor with two vector loads
+    __shared__ float sQ[D == 2 ? NC : 1][D == 2 ? NS : 1];
+    __shared__ float4 sQa[D == 3 ? NS : 1];
+    __shared__ float2 sQb[D == 3 ? NS : 1];
+    // component c (qcomp order) of Q at slot m
+    auto qc = [&](int c, int m) -> float {
+        if constexpr (D == 2) return sQ[c][m];
+        else return c == 0 ? sQa[m].x : c == 1 ? sQa[m].y : c == 2 ? sQa[m].z : c == 3 ? sQa[m].w
+                    : c == 4 ? sQb[m].x : sQb[m].y;
+    };
     __shared__ float smu[NS];
     __shared__ uint8_t stype[NS];
     __shared__ uint8_t srt[NR];               // node flags of the tile + halo 2
@@ -591,23 +602,26 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
         if (stype[k] & TLB_SOLID) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) sQ[c][k] = 0.f;
+            for (int c = 0; c < NC; ++c) {
+                if constexpr (D == 2) sQ[c][k] = 0.f;
+            }
+            if constexpr (D == 3) {
+                sQa[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sQb[k] = make_float2(0.f, 0.f);
+            }
             smu[k] = 0.f;
             continue;
         }
         Thermo<D> t = node_thermo<D, RX, RY>(p, srho, sphi, lx + 1, ly + 1, lz + (D == 3 ? 1 : 0));
         float r0 = srho[(lx + 1) + RX * ((ly + 1) + RY * (lz + (D == 3 ? 1 : 0)))];
-        if (D == 2) {
+        if constexpr (D == 2) {
             sQ[0][k] = r0 * (1.0f / 3.0f) - t.P[0];
             sQ[1][k] = r0 * (1.0f / 3.0f) - t.P[1];
             sQ[2][k] = -t.P[3];
         } else {
-            sQ[0][k] = r0 * (1.0f / 3.0f) - t.P[0];
-            sQ[1][k] = r0 * (1.0f / 3.0f) - t.P[1];
-            sQ[2][k] = r0 * (1.0f / 3.0f) - t.P[2];
-            sQ[3][k] = -t.P[3];
-            sQ[4][k] = -t.P[4];
-            sQ[5][k] = -t.P[5];
+            sQa[k] = make_float4(r0 * (1.0f / 3.0f) - t.P[0], r0 * (1.0f / 3.0f) - t.P[1],
+                                 r0 * (1.0f / 3.0f) - t.P[2], -t.P[3]);
+            sQb[k] = make_float2(-t.P[4], -t.P[5]);
         }
         smu[k] = t.mup;
     }
@@ -647,12 +661,21 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         for (int i = 1; i < Q; ++i) {
             const int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
             const float w3 = 3.0f * wt<D>(i);
+            float q[NC];
+            if constexpr (D == 2) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) q[c] = sQ[c][m];
+            } else {
+                const float4 qa = sQa[m];
+                const float2 qb = sQb[m];
+                q[0] = qa.x; q[1] = qa.y; q[2] = qa.z; q[3] = qa.w; q[4] = qb.x; q[5] = qb.y;
+            }
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 float acc = 0.f;
 #pragma unroll
                 for (int gdir = 0; gdir < D; ++gdir)
-                    if (cc<D>(i, gdir) != 0) acc += (float)cc<D>(i, gdir) * sQ[qcomp<D>(a, gdir)][m];
+                    if (cc<D>(i, gdir) != 0) acc += (float)cc<D>(i, gdir) * q[qcomp<D>(a, gdir)];
                 F[a] += w3 * acc;
             }
         }
@@ -669,7 +692,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                     if (stype[m] & TLB_SOLID) continue;
                     float wc = 6.0f * wt<D>(i) * (float)cc<D>(i, gdir);
 #pragma unroll
-                    for (int a = 0; a < D; ++a) F[a] += wc * (sQ[qcomp<D>(a, gdir)][m] - sQ[qcomp<D>(a, gdir)][sc]);
+                    for (int a = 0; a < D; ++a) F[a] += wc * (qc(qcomp<D>(a, gdir), m) - qc(qcomp<D>(a, gdir), sc));
                 }
             } else {
 #pragma unroll
@@ -687,7 +710,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                     }
                     float wc = 3.0f * wt<D>(i) * (float)cc<D>(i, gdir);
 #pragma unroll
-                    for (int a = 0; a < D; ++a) F[a] += wc * sQ[qcomp<D>(a, gdir)][m];
+                    for (int a = 0; a < D; ++a) F[a] += wc * qc(qcomp<D>(a, gdir), m);
                 }
             }
         }
