@@ -33,7 +33,7 @@ extern "C" {
 #define TLB_E_NOMEM        -2   /* device or host allocation failed */
 #define TLB_E_CUDA         -3   /* a CUDA runtime call failed */
 #define TLB_E_UNSUPPORTED  -4   /* valid request this library does not implement */
-#define TLB_E_UNCALIBRATED -5   /* force wetting with angles != 90 deg and no kappa^w */
+#define TLB_E_UNCALIBRATED -5   /* force wetting: angles != 90 deg, no kappa^w and no matching calibration */
 #define TLB_E_DIVERGED     -6   /* a non-positive density or population was met */
 #define TLB_E_TIMEOUT      -7   /* a bounded device wait gave up */
 #define TLB_E_BUSY         -8   /* no capacity (server queue or memory budget) */
@@ -94,12 +94,30 @@ int tlb_params_default(tlb_params *p);
  * phases, which must be equal (one beta, Sec. II.C) else TLB_E_UNSUPPORTED;
  * angles_deg = {theta_21, theta_31, theta_23}.  The density ratio fixes the
  * temperature of the Carnahan-Starling EOS; a and b are scaled so that the
- * coexistence densities are the ones given.  Force wetting with any angle
- * other than 90 deg needs explicit strengths (tlb_create_ex): it returns
- * TLB_E_UNCALIBRATED here. */
+ * coexistence densities are the ones given.  Force wetting takes its
+ * strengths from a registered calibration table (tlb_set_force_calibration)
+ * when an angle differs from 90 deg; without a matching table, or outside
+ * its range, the call returns TLB_E_UNCALIBRATED. */
 int tlb_create(int lattice, int nx, int ny, int nz, const double densities[2], const double kappas[3],
                const double viscosities[3], int wetting, const double angles_deg[3], tlb_ctx **out);
 int tlb_create_ex(const tlb_params *p, tlb_ctx **out);
+
+/* Force-wetting calibration.  Eq. forceBC (Sec. IV) sets the wall's wetting
+ * through strengths kappa^w, not angles; the paper maps one to the other by
+ * measurement.  This registers such a measurement: n pairs (kappa_w[i],
+ * theta_deg[i]) of a liquid drop on a wall (kappa_phi^w = 0), kappa_w
+ * increasing and theta decreasing, for the lattice and thermodynamic
+ * parameter set of *p (lattice, lambda, kappa, chi, a, b, R, rho_l, rho_g;
+ * the other fields are ignored).  tlb_create / tlb_create_ex / tlb_submit with
+ * TLB_WET_FORCE, kw_rho = kw_phi = 0 and theta_21 or theta_31 != 90 deg then
+ * set s2 = kappa(theta_21), s3 = kappa(theta_31) by linear interpolation and
+ * kw_rho = (s2 + s3)/2, kw_phi = (s2 - s3)/2 (theta_23 is not an input of this
+ * scheme).  Explicit kw_rho / kw_phi always take precedence.  Tables are
+ * process-wide; registering the same lattice and parameter set again
+ * replaces its table.  Host data, copied.  TLB_E_INVAL for fewer than two
+ * points, non-finite or non-monotone data.  The Python binding registers the
+ * tables shipped in paper_1904_06881_gb300/force_wetting_calibration.json. */
+int tlb_set_force_calibration(const tlb_params *p, const double *kappa_w, const double *theta_deg, int n);
 void tlb_destroy(tlb_ctx *ctx);
 int tlb_get_params(const tlb_ctx *ctx, tlb_params *out);
 int tlb_get_derived(const tlb_ctx *ctx, tlb_derived *out);

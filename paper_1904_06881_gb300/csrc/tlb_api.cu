@@ -52,7 +52,7 @@ extern "C" const char *tlb_strerror(int code)
     case TLB_E_NOMEM: return "out of memory";
     case TLB_E_CUDA: return "CUDA error";
     case TLB_E_UNSUPPORTED: return "unsupported";
-    case TLB_E_UNCALIBRATED: return "force wetting needs kappa^w for angles other than 90 deg";
+    case TLB_E_UNCALIBRATED: return "force wetting: no kappa^w and no calibration for the angles";
     case TLB_E_DIVERGED: return "non-positive density or population";
     case TLB_E_TIMEOUT: return "device wait timed out";
     case TLB_E_BUSY: return "busy";
@@ -458,11 +458,101 @@ static int validate(const tlb_params &p)
         field = (decltype(field))p_;                                     \
     } while (0)
 
+// ---------------------------------------------------------------------------
+// Force-wetting calibration (no counterpart in the paper, whose wetting force
+// of Eq. forceBC takes strengths, not angles): registered tables of measured
+// (kappa^w, theta) pairs of a liquid drop on a wall, per lattice and
+// thermodynamic parameter set.
+// ---------------------------------------------------------------------------
+namespace {
+struct ForceTable {
+    tlb_params key;
+    std::vector<double> kw, th;      // th strictly decreasing in kw
+};
+std::mutex g_cal_mutex;
+std::vector<ForceTable> g_cal;
+
+bool same_set(const tlb_params &a, const tlb_params &b)
+{
+    auto eq = [](double x, double y) { return std::fabs(x - y) <= 1e-9 * std::max(1.0, std::fabs(x)); };
+    if (a.lattice != b.lattice) return false;
+    for (int k = 0; k < 3; ++k)
+        if (!eq(a.lambda[k], b.lambda[k]) || !eq(a.kappa[k], b.kappa[k])) return false;
+    return eq(a.chi, b.chi) && eq(a.rho_l, b.rho_l) && eq(a.rho_g, b.rho_g) && eq(a.a, b.a) && eq(a.b, b.b) &&
+           eq(a.R, b.R);
+}
+
+// strength for angle th by linear interpolation in the table; false outside it
+bool table_kw(const ForceTable &t, double th, double &kw)
+{
+    const size_t n = t.th.size();
+    if (!(th <= t.th.front() && th >= t.th.back())) return false;
+    for (size_t i = 0; i + 1 < n; ++i)
+        if (th <= t.th[i] && th >= t.th[i + 1]) {
+            const double s = (t.th[i] - th) / (t.th[i] - t.th[i + 1]);
+            kw = t.kw[i] + s * (t.kw[i + 1] - t.kw[i]);
+            return true;
+        }
+    return false;
+}
+
+// Force wetting with angles and no strengths: the liquid-gas angles theta_21
+// (liquid 2) and theta_31 (liquid 3) map to the strengths s2, s3 of the two
+// liquids, kappa_rho^w = (s2 + s3)/2, kappa_phi^w = (s2 - s3)/2 (rho^rel = 1,
+// phi^rel = +-1 in Eq. forceBC).  theta_23 is not an input of this scheme.
+int apply_force_calibration(tlb_params &p)
+{
+    if (p.wetting != TLB_WET_FORCE || p.kw_rho != 0.0 || p.kw_phi != 0.0) return TLB_OK;
+    if (p.theta_deg[0] == 90.0 && p.theta_deg[1] == 90.0) return TLB_OK;
+    std::lock_guard<std::mutex> lk(g_cal_mutex);
+    for (const ForceTable &t : g_cal) {
+        if (!same_set(t.key, p)) continue;
+        double s2 = 0.0, s3 = 0.0;
+        if (!table_kw(t, p.theta_deg[0], s2) || !table_kw(t, p.theta_deg[1], s3))
+            return fail(TLB_E_UNCALIBRATED, "force wetting: angles (%g, %g) outside the calibrated range [%g, %g] deg",
+                        p.theta_deg[0], p.theta_deg[1], t.th.back(), t.th.front());
+        p.kw_rho = 0.5 * (s2 + s3);
+        p.kw_phi = 0.5 * (s2 - s3);
+        return TLB_OK;
+    }
+    return fail(TLB_E_UNCALIBRATED, "force wetting: no calibration table for this lattice and parameter set "
+                                    "(pass kw_rho, kw_phi, or register one with tlb_set_force_calibration)");
+}
+}  // namespace
+
+extern "C" int tlb_set_force_calibration(const tlb_params *p, const double *kappa_w, const double *theta_deg, int n)
+{
+    if (!p || !kappa_w || !theta_deg) return fail(TLB_E_INVAL, "null argument");
+    if (n < 2) return fail(TLB_E_INVAL, "a calibration table needs at least two points");
+    ForceTable t;
+    t.key = *p;
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(kappa_w[i]) || !std::isfinite(theta_deg[i]))
+            return fail(TLB_E_INVAL, "non-finite calibration point %d", i);
+        if (i > 0 && !(kappa_w[i] > kappa_w[i - 1] && theta_deg[i] < theta_deg[i - 1]))
+            return fail(TLB_E_INVAL, "calibration points must increase in kappa^w and decrease in theta (point %d)", i);
+        t.kw.push_back(kappa_w[i]);
+        t.th.push_back(theta_deg[i]);
+    }
+    std::lock_guard<std::mutex> lk(g_cal_mutex);
+    for (ForceTable &u : g_cal)
+        if (same_set(u.key, *p)) {
+            u = t;
+            return TLB_OK;
+        }
+    g_cal.push_back(t);
+    return TLB_OK;
+}
+
 extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
 {
     if (!pin || !out) return fail(TLB_E_INVAL, "null argument");
     *out = nullptr;
-    int rc = validate(*pin);
+    tlb_params pc = *pin;
+    int rc = apply_force_calibration(pc);
+    if (rc) return rc;
+    pin = &pc;
+    rc = validate(*pin);
     if (rc) return rc;
     tlb_ctx *c = new tlb_ctx();
     c->p = *pin;
@@ -563,11 +653,7 @@ extern "C" int tlb_create(int lattice, int nx, int ny, int nz, const double dens
     p.beta = 1.0 / (1.0 + 6.0 * viscosities[0]);   // nu = (1/beta - 1)/6
     p.wetting = wetting;
     for (int k = 0; k < 3; ++k) p.theta_deg[k] = angles_deg[k];
-    if (wetting == TLB_WET_FORCE)
-        for (int k = 0; k < 3; ++k)
-            if (angles_deg[k] != 90.0)
-                return fail(TLB_E_UNCALIBRATED, "force wetting: pass kappa^w through tlb_create_ex for angles != 90");
-    return tlb_create_ex(&p, out);
+    return tlb_create_ex(&p, out);      // force wetting: angles through the calibration tables
 }
 
 extern "C" void tlb_destroy(tlb_ctx *c)

@@ -32,6 +32,7 @@ ENTRY_POINTS = (
     "tlb_lattice_directions", "tlb_snapshot_bytes", "tlb_snapshot", "tlb_restore", "tlb_steps_done",
     "tlb_device_bytes", "tlb_launch_count", "tlb_step_batch", "tlb_server_create", "tlb_submit",
     "tlb_server_pump", "tlb_poll", "tlb_server_stats", "tlb_server_destroy", "tlb_step_noalloc",
+    "tlb_set_force_calibration",
 )
 
 
@@ -123,13 +124,43 @@ def lib():
         "tlb_server_stats": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz)]),
         "tlb_server_destroy": (None, [vp]),
         "tlb_step_noalloc": (i, [ctypes.POINTER(Params), u8p, vp, vp, vp, vp, i, vp]),
+        "tlb_set_force_calibration": (i, [ctypes.POINTER(Params), dp, dp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
     _lib = L
+    register_force_calibration()
     return L
+
+
+CALIBRATION_PATH = os.path.join(_HERE, "force_wetting_calibration.json")
+
+
+def tlb_set_force_calibration(params, kappa_w, theta_deg):
+    kw = np.ascontiguousarray(kappa_w, dtype=np.float64)
+    th = np.ascontiguousarray(theta_deg, dtype=np.float64)
+    return _check(lib().tlb_set_force_calibration(ctypes.byref(params), _dptr(kw), _dptr(th), len(kw)),
+                  "tlb_set_force_calibration")
+
+
+def register_force_calibration(path=None):
+    """Register the force-wetting calibration tables of a JSON file (default:
+    the tables shipped with the package, written by calibrate.py) with the
+    library; returns the number of tables.  A missing default file registers
+    nothing."""
+    path = CALIBRATION_PATH if path is None else path
+    if not os.path.exists(path):
+        return 0
+    import json
+
+    with open(path) as fh:
+        tables = json.load(fh)["tables"]
+    for t in tables:
+        p = make_params(t["lattice"], 8, 8, 1 if t["lattice"] == D2Q9 else 8, **t["params"])
+        tlb_set_force_calibration(p, t["kappa_w"], t["theta_deg"])
+    return len(tables)
 
 
 def _check(rc, where):

@@ -190,6 +190,18 @@ def big_periodic_drop_2d(n=4096, R=None):
                 mask=np.zeros((1, n, n), np.uint8), rho=rho[None], phi=phi[None], steps=1000)
 
 
+def big_periodic_drop_3d(n=256, R=None):
+    """Large D3Q27 periodic lattice with one liquid-1 drop (no walls)."""
+    R = n / 4.0 if R is None else R
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(np.float32)
+    d = np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2 + (z - n / 2) ** 2).astype(np.float64)
+    del x, y, z
+    C2 = _blob(d, R, 2.0)
+    rho, phi = phase_fields(C2, np.zeros_like(C2))
+    return dict(name="big_d3q27_%d" % n, lattice=D3Q27, nx=n, ny=n, nz=n, params=base_params(),
+                mask=np.zeros((n, n, n), np.uint8), rho=rho, phi=phi, steps=1000)
+
+
 def c4_requests(seed=4, n=64, rate=20.0):
     """Served mix: Poisson arrivals (mean `rate` per second) of requests drawn
     from sessile drops (64^2-256^2), capillary channels (256x64-1024x64) and

@@ -236,8 +236,9 @@ def _tiny(lattice, nx, ny, nz, wet, R):
         mask = np.zeros((nz, ny, nx), np.uint8)
         mask[0] = 1
         mask[nz - 1] = 1
-    return dict(name="tiny", lattice=lattice, nx=nx, ny=ny, nz=nz,
-                params=W.base_params(wetting=wet, theta_deg=(60.0, 60.0, 120.0)),
+    params = (W.base_params(wetting=wet, kw_rho=0.05) if wet == W.WET_FORCE
+              else W.base_params(wetting=wet, theta_deg=(60.0, 60.0, 120.0)))
+    return dict(name="tiny", lattice=lattice, nx=nx, ny=ny, nz=nz, params=params,
                 mask=mask, rho=rho, phi=phi, steps=100)
 
 
