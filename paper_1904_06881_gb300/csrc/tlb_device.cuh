@@ -4,19 +4,22 @@
 //
 // Data layout in HBM (one lattice of N nodes, x fastest, periodic):
 //   f  : float[Q][N]  pre-collision populations stored as f_i - w_i
-//   g  : float[Q][N]  (or half[Q][N] scaled by 1/chi) order-parameter populations
-//   rho, phi : float[N] moments of the current state; solid ghost nodes hold
-//              the ghost-layer values of Sec. IV
-//   type : uint8[N]  node flags (TLB_SOLID, TLB_FIRST, TLB_GHOST, wall axes)
-// One step = two launches (the same kernels for one lattice and for a batch,
-// through a tile -> lattice table):
-//   moments_batch_kernel : rho = 1 + sum_i f~_i, phi = sum_i g_i  (reads 2Q values)
-//   step_batch_kernel    : tile + halo 2 of rho, phi in shared memory, ghost
-//                          layer filled there from the fluid moments -> stencils,
-//                          chemical potentials, pressure tensor (halo 1) -> force
-//                          with wall rules -> ELBM collision of f (entropic
-//                          alpha), LBGK of g -> push streaming with halfway
-//                          bounce-back.
+//   g  : float[Q][N], or (reduced precision) g_0 as float[N] followed by the
+//        moving populations as half[Q-1][N] scaled by 16
+//   rho, phi : float[N] moments of the current state, written by the moments
+//              kernel (ghost values are computed in shared memory by the step
+//              kernels; only the auxiliary-output and allocation-free paths
+//              write them to these arrays)
+//   type : uint8[N]  node flags (TLB_SOLID, TLB_FIRST, TLB_GHOST, TLB_NEAR, wall axes)
+// One step, through a tile -> lattice table (the same kernels for one lattice
+// and for a batch):
+//   D2Q9  : step_batch_kernel alone -- rho, phi of the tile + halo 2 summed
+//           from the populations, ghost layer, stencils, chemical potentials,
+//           pressure tensor (halo 1), force with wall rules, ELBM collision of
+//           f (entropic alpha), LBGK of g, push streaming with halfway
+//           bounce-back;
+//   D3Q27 : moments_batch_kernel (rho = 1 + sum_i f~_i, phi = sum_i g_i), then
+//           step_batch_kernel as above with rho, phi read from the moments.
 #pragma once
 #include <cuda_fp16.h>
 #include <stdint.h>
