@@ -57,7 +57,7 @@ def test_invalid_arguments_rejected_on_host(L):
     assert e.value.code == -4          # unequal viscosities: one beta only
     with pytest.raises(tlb.TlbError) as e:
         tlb.tlb_create(tlb.D2Q9, 64, 64, 1, (1.0, 1e-3), (0.01, 1, 1), (1 / 6,) * 3, tlb.WET_FORCE, (60, 90, 90))
-    assert e.value.code == -5          # force wetting needs explicit kappa^w
+    assert e.value.code == -5          # force wetting: no calibration table for this parameter set
     with pytest.raises(tlb.TlbError) as e:
         tlb.tlb_create(tlb.D2Q9, 2, 64, 1, (1.0, 1e-3), (0.01, 1, 1), (1 / 6,) * 3, tlb.WET_FORCE, (90, 90, 90))
     assert e.value.code == -1
