@@ -259,3 +259,30 @@ def test_lattices_smaller_than_a_tile(lattice, nx, ny, nz, wet, R):
     e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
     for k in ("rho", "phi", "C"):
         assert e[k] <= max(TOL, 3 * ref[k]), (e, ref)
+
+
+@pytest.mark.parametrize("case", ["c0_force", "c1_channel", "d3q27"])
+def test_diagnostics_match_oracle(case):
+    """Row a9: the FP64 diagnostics (masses of rho and phi, total
+    concentrations, kinetic energy) of the same populations.  The GPU sums
+    FP32 moments in FP64, so each node contributes at most a few FP32
+    roundings of its own scale: the bound is N * 4 * 2^-24 times rho_l (mass
+    of rho), chi (mass of phi), rho_l / (rho_l - rho_g) + 1 (concentrations);
+    the kinetic energy within 1e-5 of its value.  A dropped node or a wrong
+    term would be off by O(1) per node."""
+    wl = {"c0_force": W.c0_sessile_drop, "c1_channel": W.c1_capillary, "d3q27": _small3d}[case]()
+    g, o = _pair(wl)
+    g.step(200)
+    perm = match_directions(wl["lattice"])
+    fg, gg = g.populations()
+    o.set_populations(fg[perm], gg[perm])
+    dg, do = g.diagnostics(), o.diagnostics()
+    d = o.derived
+    N = int((wl["mask"] == 0).sum())
+    ulp = 4 * 2.0 ** -24
+    scale = dict(mass_rho=d["rho_l"], mass_phi=wl["params"]["chi"])
+    for k in ("C1", "C2", "C3"):
+        scale[k] = d["rho_l"] / (d["rho_l"] - d["rho_g"]) + 1.0
+    for k, sc in scale.items():
+        assert abs(dg[k] - do[k]) <= N * ulp * sc, (k, dg[k], do[k])
+    assert abs(dg["kinetic"] - do["kinetic"]) <= 1e-5 * abs(do["kinetic"]) + 1e-12, (dg["kinetic"], do["kinetic"])
