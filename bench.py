@@ -31,13 +31,14 @@ L2_FLUSH_BYTES = 256 << 20
 
 
 def kernel_source_hash():
-    """sha256 over the kernel sources (csrc/*.cu, *.cuh, *.h), in name order."""
+    """sha256 over the device-code sources (csrc/*.cuh, *.h and the per-lattice
+    kernel units; not the host-side tlb_api.cu), in name order."""
     import glob
     import hashlib
 
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_1904_06881_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")) and os.path.basename(f) != "tlb_api.cu":
             h.update(os.path.basename(f).encode())
             with open(f, "rb") as fh:
                 h.update(fh.read())

@@ -13,6 +13,19 @@
 #include <deque>
 #include <map>
 #include <mutex>
+
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range for the duration of a scope: host-side API calls show up by name
+// in Nsight Systems timelines (a few nanoseconds when no tool is attached)
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 #include <string>
 #include <vector>
 
@@ -884,6 +897,7 @@ static int capture_step(tlb_ctx *c)
 
 extern "C" int tlb_step(tlb_ctx *c, int nsteps)
 {
+    NvtxRange range("tlb_step");
     if (!c) return fail(TLB_E_INVAL, "null context");
     if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
     const int per = launches_per_step(c->D);
@@ -1198,6 +1212,7 @@ static int run_plan(BatchPlan &plan, int nsteps, cudaStream_t st)
 
 extern "C" int tlb_step_batch(tlb_ctx *const *ctxs, int n, int nsteps)
 {
+    NvtxRange range("tlb_step_batch");
     if (!ctxs || n <= 0 || nsteps < 0) return fail(TLB_E_INVAL, "bad batch arguments");
     for (int k = 0; k < n; ++k)
         if (!ctxs[k]) return fail(TLB_E_INVAL, "null context in batch");
@@ -1312,9 +1327,11 @@ static void retire(tlb_server *s, Req *q, int status)
 extern "C" int tlb_server_pump(tlb_server *s)
 {
     if (!s) return fail(TLB_E_INVAL, "null server");
+    NvtxRange range("tlb_server_pump");
     std::lock_guard<std::mutex> lk(s->mu);
     // admit in arrival order while memory and slots allow (no overtaking)
     while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
+        NvtxRange admit("tlb_server admit");
         Req *q = s->queue.front();
         if (s->in_use + q->bytes > s->budget) break;
         s->queue.pop_front();
@@ -1414,6 +1431,7 @@ NoallocDevice g_noalloc_dev[64];
 extern "C" int tlb_step_noalloc(const tlb_params *p, const uint8_t *mask, float *f, float *f_tmp, void *g,
                                 void *g_tmp, int nsteps, void *cuda_stream)
 {
+    NvtxRange range("tlb_step_noalloc");
     if (!p || !f || !f_tmp || !g || !g_tmp) return fail(TLB_E_INVAL, "null argument");
     if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
     int rc = validate(*p);
