@@ -38,6 +38,8 @@ extern "C" {
 #define TLB_E_TIMEOUT      -7   /* a bounded device wait gave up */
 #define TLB_E_BUSY         -8   /* no capacity (server queue or memory budget) */
 #define TLB_E_NOTFOUND     -9   /* unknown ticket */
+#define TLB_E_BOUNDS      -10   /* bounds-checked builds (-DTLB_BOUNDS_CHECK) only: a kernel computed a
+                                   node index outside its array; the access was skipped */
 
 enum { TLB_D2Q9 = 0, TLB_D3Q27 = 1 };
 enum { TLB_WET_FORCE = 0, TLB_WET_GEOM_EXTRAP = 1, TLB_WET_GEOM_INTERP = 2 };

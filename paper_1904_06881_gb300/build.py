@@ -3,6 +3,14 @@
 The library lands in paper_1904_06881_gb300/_build/libtlb.so.  Three
 translation units (host ABI, D2Q9 kernels, D3Q27 kernels) compile in
 parallel; only files newer than their object are rebuilt.
+
+build(check=True) makes the bounds-checked variant in _build_check/: every
+node index a kernel computes is tested against the lattice size, a bad one
+is recorded and its access skipped, and tlb_sync reports TLB_E_BOUNDS.  It
+is a test build (slower; the normal library is the product).  Load it with
+TLB_LIBRARY=<path> in the environment.
+
+    python -m paper_1904_06881_gb300.build [--force] [--check]
 """
 import os
 import subprocess
@@ -13,6 +21,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtlb.so")
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(BUILD_CHECK, "libtlb.so")
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--use_fast_math", "-diag-suppress", "177"]
@@ -31,18 +41,20 @@ def _newest(paths):
     return max(os.path.getmtime(p) for p in paths if os.path.exists(p))
 
 
-def build(verbose=False, force=False):
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, force=False, check=False):
+    bdir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
+    extra = ["-DTLB_BOUNDS_CHECK"] if check else []
+    os.makedirs(bdir, exist_ok=True)
     deps = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "tlb.h")]
     dep_time = _newest(deps)
     nvcc = _nvcc()
 
     def compile_one(src):
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         if not force and os.path.exists(o) and os.path.getmtime(o) >= max(dep_time, os.path.getmtime(s)):
             return o
-        cmd = [nvcc] + ARCH + FLAGS + ["-I", os.path.join(ROOT, "include"), "-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc] + ARCH + FLAGS + extra + ["-I", os.path.join(ROOT, "include"), "-c", s, "-o", o + ".tmp"]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.check_call(cmd)
@@ -51,12 +63,12 @@ def build(verbose=False, force=False):
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
-        tmp = LIB + ".%d.tmp" % os.getpid()
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < _newest(objs):
+        tmp = lib + ".%d.tmp" % os.getpid()
         subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, check="--check" in sys.argv))

@@ -69,6 +69,7 @@ extern "C" const char *tlb_strerror(int code)
     case TLB_E_DIVERGED: return "non-positive density or population";
     case TLB_E_TIMEOUT: return "device wait timed out";
     case TLB_E_BUSY: return "busy";
+    case TLB_E_BOUNDS: return "index outside its array (bounds-checked build)";
     case TLB_E_NOTFOUND: return "unknown ticket";
     default: return "unknown error";
     }
@@ -787,6 +788,14 @@ static int check_status(tlb_ctx *c)
         c->sticky = TLB_E_DIVERGED;
         return fail(TLB_E_DIVERGED, "non-positive density or population met");
     }
+#ifdef TLB_BOUNDS_CHECK
+    // the error words are per lattice type, not per context: a violation shows
+    // at the next check of any context
+    if (unsigned nb = Launch<2>::bounds_errors() | Launch<3>::bounds_errors()) {
+        c->sticky = TLB_E_BOUNDS;
+        return fail(TLB_E_BOUNDS, "bounds check: %u flagged node indices outside their arrays", nb);
+    }
+#endif
     return TLB_OK;
 }
 

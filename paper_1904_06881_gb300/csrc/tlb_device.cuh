@@ -89,9 +89,29 @@ __device__ __forceinline__ int wrapi(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+// Bounds-checked builds (-DTLB_BOUNDS_CHECK): every node index the kernels
+// compute passes through chk_node; one outside [0, N) sets this translation
+// unit's error word (read by Launch<D>::bounds_errors) and is replaced by 0,
+// so the access stays inside the array.  Without the flag chk_node is the
+// identity.
+#ifdef TLB_BOUNDS_CHECK
+static __device__ unsigned g_bounds_error;
+__device__ __forceinline__ long long chk_node(long long n, const DevParams &p)
+{
+    if (n < 0 || n >= p.N) {
+        atomicOr(&g_bounds_error, 1u);
+        return 0;
+    }
+    return n;
+}
+#else
+__device__ __forceinline__ long long chk_node(long long n, const DevParams &) { return n; }
+#endif
+
 __device__ __forceinline__ long long node_of(const DevParams &p, int x, int y, int z)
 {
-    return (long long)wrapi(x, p.nx) + (long long)p.nx * ((long long)wrapi(y, p.ny) + (long long)p.ny * wrapi(z, p.nz));
+    return chk_node(
+        (long long)wrapi(x, p.nx) + (long long)p.nx * ((long long)wrapi(y, p.ny) + (long long)p.ny * wrapi(z, p.nz)), p);
 }
 
 // ---------------------------------------------------------------------------

@@ -81,6 +81,9 @@ struct Launch {
     static void diagnostics(const DevParams &p, const DevState &s, double *partials, int nblocks, double *out,
                             cudaStream_t st);
     static int diag_blocks(const DevParams &p);
+    // bounds-checked builds: the number of flagged index errors of this lattice
+    // type's kernels since the last call (which resets it); 0 otherwise
+    static unsigned bounds_errors();
     static void convert_pop(const DevParams &p, const DevState &s, int dir, double *fbuf, double *gbuf,
                             cudaStream_t st);
     // batched: entries[0..n) and a tile table (tile -> entry, tile coords)

@@ -59,7 +59,8 @@ __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >
 
 __device__ __forceinline__ long long node_near(const DevParams &p, int x, int y, int z)
 {
-    return (long long)wrap1(x, p.nx) + (long long)p.nx * ((long long)wrap1(y, p.ny) + (long long)p.ny * wrap1(z, p.nz));
+    return chk_node(
+        (long long)wrap1(x, p.nx) + (long long)p.nx * ((long long)wrap1(y, p.ny) + (long long)p.ny * wrap1(z, p.nz)), p);
 }
 
 // Programmatic dependent launch: a stepping kernel lets the next one be
@@ -648,7 +649,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         int xx = cx == 0 ? x : (cx > 0 ? xq : xm);
         int yy = cy == 0 ? y : (cy > 0 ? yq : ym);
         int zz = cz == 0 ? z : (cz > 0 ? zq : zm);
-        return (long long)xx + (long long)p.nx * ((long long)yy + (long long)p.ny * zz);
+        return chk_node((long long)xx + (long long)p.nx * ((long long)yy + (long long)p.ny * zz), p);
     };
     const float r = srho[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
     const float ph = sphi[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
@@ -1139,6 +1140,19 @@ static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t sme
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <int D>
+unsigned Launch<D>::bounds_errors()
+{
+#ifdef TLB_BOUNDS_CHECK
+    unsigned v = 0, zero = 0;
+    cudaMemcpyFromSymbol(&v, g_bounds_error, sizeof(v));
+    cudaMemcpyToSymbol(g_bounds_error, &zero, sizeof(zero));
+    return v;
+#else
+    return 0;
+#endif
 }
 
 template <int D>

@@ -13,12 +13,14 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libtlb.so")
+# TLB_LIBRARY selects another build of the same library (the bounds-checked
+# one, build(check=True)); it must export the same entry points
+LIB_PATH = os.environ.get("TLB_LIBRARY") or os.path.join(_HERE, "_build", "libtlb.so")
 
 TLB_OK = 0
 ERRORS = {-1: "TLB_E_INVAL", -2: "TLB_E_NOMEM", -3: "TLB_E_CUDA", -4: "TLB_E_UNSUPPORTED",
           -5: "TLB_E_UNCALIBRATED", -6: "TLB_E_DIVERGED", -7: "TLB_E_TIMEOUT", -8: "TLB_E_BUSY",
-          -9: "TLB_E_NOTFOUND"}
+          -9: "TLB_E_NOTFOUND", -10: "TLB_E_BOUNDS"}
 D2Q9, D3Q27 = 0, 1
 WET_FORCE, WET_GEOM_EXTRAP, WET_GEOM_INTERP = 0, 1, 2
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
