@@ -2,6 +2,8 @@
 // derivation (Carnahan-Starling coexistence, Sec. II.A), mask preprocessing
 // (ghost layer, wall flags, Sec. IV), buffers, kernel launches, batched
 // stepping and the request server.
+#include <cuda.h>            // CUtensorMap and its enums; the encoder is looked up at run time
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -402,6 +404,7 @@ struct tlb_ctx {
     long long launches = 0;
     int sticky = TLB_OK;
     // the lattice as a batch of one: entries for both buffer parities, tile table
+    CUtensorMap *tmaps = nullptr;     // D3Q27: per parity, tensor maps of f_in and g_in (null if unused)
     BatchEntry *self_entries = nullptr;
     int4 *self_tiles = nullptr;
     int nself_tiles = 0;
@@ -471,6 +474,74 @@ static int validate(const tlb_params &p)
         if (rc) { dev_free_all(c->owned); delete c; return rc; }         \
         field = (decltype(field))p_;                                     \
     } while (0)
+
+// cuTensorMapEncodeTiled from the driver, looked up once (the library does not
+// link against libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    });
+    return fn;
+}
+
+// D3Q27: tensor maps of both parities' input populations, for the step
+// kernel's TMA copies of a tile's own nodes (a box of TX x TY x TZ nodes and
+// all directions; the copy lands in the layout [direction][z][y][x] of the
+// staging area).  Per parity: f, then FP32 g, or the FP32 rest channel of g and
+// its FP16 moving channels.  Every global stride must be a multiple of 16
+// bytes: nx % 4 == 0 (FP32 arrays), nx % 8 == 0 (FP16 channels).  Returns false
+// when the lattice does not qualify or the driver offers no encoder; the kernel
+// then copies with per-thread cp.async.
+static bool encode_tensor_maps(const tlb_ctx *c, CUtensorMap maps[6])
+{
+    if (c->D != 3) return false;
+    const bool half = c->p.g_fp16 != 0;
+    const cuuint64_t nx = c->p.nx, ny = c->p.ny, nz = c->p.nz, N = (cuuint64_t)c->N;
+    if (nx % (half ? 8 : 4) != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint32_t box[4] = {(cuuint32_t)Launch<3>::tile_dims(0), (cuuint32_t)Launch<3>::tile_dims(1),
+                               (cuuint32_t)Launch<3>::tile_dims(2), 0};
+    auto tiled = [&](CUtensorMap *m, CUtensorMapDataType dt, cuuint64_t esz, const void *base, cuuint32_t depth) {
+        if ((uintptr_t)base & 15) return false;
+        const cuuint32_t rank = depth > 1 ? 4 : 3;
+        const cuuint64_t dims[4] = {nx, ny, nz, depth};
+        const cuuint64_t strides[3] = {nx * esz, nx * ny * esz, N * esz};
+        const cuuint32_t b[4] = {box[0], box[1], box[2], depth};
+        const cuuint32_t one[4] = {1, 1, 1, 1};
+        return enc(m, dt, rank, const_cast<void *>(base), dims, strides, b, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    memset(maps, 0, 6 * sizeof(CUtensorMap));
+    const cuuint32_t Q = (cuuint32_t)c->Q;
+    for (int par = 0; par < 2; ++par) {
+        CUtensorMap *m = maps + 3 * par;
+        if (!tiled(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->s.f[par], Q)) return false;
+        if (!half) {
+            if (!tiled(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->s.g[par], Q)) return false;
+        } else {
+            if (!tiled(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->s.g[par], 1)) return false;
+            if (!tiled(&m[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (const char *)c->s.g[par] + 4 * N, Q - 1))
+                return false;
+        }
+    }
+    return true;
+}
+
+// the entry's tensor-map pointers for input buffer `cur` (all null without maps)
+static void entry_maps(const tlb_ctx *c, int cur, BatchEntry &e)
+{
+    for (int k = 0; k < 3; ++k) e.tm[k] = c->tmaps ? (const void *)(c->tmaps + 3 * cur + k) : nullptr;
+}
 
 // ---------------------------------------------------------------------------
 // Force-wetting calibration (no counterpart in the paper, whose wetting force
@@ -610,6 +681,17 @@ extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
     cudaMemsetAsync(c->s.phi, 0, N * 4, c->stream);
     c->type_host.assign(N, 0);
     {
+        CUtensorMap maps[6];
+        if (encode_tensor_maps(c, maps)) {
+            ALLOC_LATE(c->tmaps, sizeof(maps));
+            if ((uintptr_t)c->tmaps & 63) {
+                c->tmaps = nullptr;           // a tensor map in global memory needs 64-byte alignment
+            } else {
+                cudaMemcpyAsync(c->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, c->stream);
+            }
+        }
+    }
+    {
         // batch-of-one tables: entry per buffer parity, one tile per CTA
         int D = c->D;
         int TX = D == 2 ? Launch<2>::tile_dims(0) : Launch<3>::tile_dims(0);
@@ -630,6 +712,7 @@ extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
             ent[par].phi = c->s.phi;
             ent[par].type = c->s.type;
             ent[par].status = c->s.status;
+            entry_maps(c, par, ent[par]);
         }
         ALLOC_LATE(c->self_entries, sizeof(ent));
         ALLOC_LATE(c->self_tiles, tiles.size() * sizeof(int4));
@@ -784,6 +867,10 @@ static int check_status(tlb_ctx *c)
     unsigned st = 0;
     CUDA_TRY(cudaMemcpyAsync(&st, c->s.status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (st & STATUS_TIMEOUT) {
+        c->sticky = TLB_E_TIMEOUT;
+        return fail(TLB_E_TIMEOUT, "a tile's tensor copies did not complete within one second");
+    }
     if (st) {
         c->sticky = TLB_E_DIVERGED;
         return fail(TLB_E_DIVERGED, "non-positive density or population met");
@@ -1174,6 +1261,7 @@ static int build_plan(tlb_ctx *const *ctxs, int n, BatchPlan &plan, cudaStream_t
             e.phi = c->s.phi;
             e.type = c->s.type;
             e.status = c->s.status;
+            entry_maps(c, cur, e);
         }
         for (int z = 0; z < c->p.nz; z += TZ)
             for (int y = 0; y < c->p.ny; y += TY)

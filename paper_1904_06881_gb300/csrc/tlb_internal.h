@@ -49,7 +49,13 @@ struct DevState {
     int *ghosts;          // ghost-node list
     int nghost;
     int cur;              // index of the current population buffer
-    unsigned *status;     // device error flags (bit 0: non-positive density/population)
+    unsigned *status;     // device error flags (STATUS_* bits)
+};
+
+// bits of the device status word
+enum : unsigned {
+    STATUS_DIVERGED = 1u,  // a non-positive density or population was met
+    STATUS_TIMEOUT = 2u,   // a bounded wait for a tile's tensor copies gave up
 };
 
 // Auxiliary outputs of the step kernel (AUX mode); any may be null.
@@ -67,6 +73,10 @@ struct BatchEntry {
     const float *rho, *phi;
     const uint8_t *type;
     unsigned *status;
+    // D3Q27 lattices whose strides allow it: tensor maps (device memory) of
+    // f_in and g_in (FP32 g) or of its FP32 rest channel and FP16 moving
+    // channels, for TMA copies of a tile's own populations; null otherwise
+    const void *tm[3];
 };
 
 // Launchers implemented per lattice (D = 2: tlb_d2q9.cu, D = 3: tlb_d3q27.cu).

@@ -78,13 +78,70 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Tensor-memory-accelerator copies (cp.async.bulk.tensor): one thread moves a
+// tile's box of every direction into shared memory; completion is counted in
+// bytes on an mbarrier that the consumers wait on.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the tensor-copy (async) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;\n"
+                 "fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0, int c1, int c2, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];\n"
+                 ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+                 ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return done != 0;
+}
+// waits for the barrier's phase `parity` to complete; false after `ns` nanoseconds
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, unsigned long long ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > ns) return false;
+    return true;
+}
+
 // dynamic shared memory of the stepping kernel: f (and FP32 g) of the tile's own nodes
 template <int D, typename GT>
 __host__ __device__ constexpr int stage_bytes()
 {
-    // f: Q floats; g: Q floats, or g_0 as a float plus Q-1 halves
+    // f: Q floats; g: Q floats, or g_0 as a float plus Q-1 halves; D3Q27: 128
+    // bytes more, to start the area on a 128-byte boundary (tensor copies)
     return Tile<D>::X * Tile<D>::Y * Tile<D>::Z *
-           (Lat<D>::Q * 4 + (sizeof(GT) == 4 ? Lat<D>::Q * 4 : 4 + (Lat<D>::Q - 1) * 2));
+               (Lat<D>::Q * 4 + (sizeof(GT) == 4 ? Lat<D>::Q * 4 : 4 + (Lat<D>::Q - 1) * 2)) +
+           (D == 3 ? 128 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -326,7 +383,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                                           const void *g_in, void *g_out, const float *__restrict__ rho,
                                           const float *__restrict__ phi, const uint8_t *__restrict__ type,
                                           unsigned *status, int x0, int y0, int z0, const float *__restrict__ u_init,
-                                          const AuxOut &aux)
+                                          const AuxOut &aux, const void *const *tm = nullptr)
 {
     constexpr int Q = Lat<D>::Q;
     constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
@@ -363,7 +420,15 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     __shared__ int nghost;
     const int tid = threadIdx.x;
     constexpr int NT = TX * TY * TZ;
-    extern __shared__ float stage[];          // ASYNC: f[Q][NT], then FP32 g[Q][NT]
+    // ASYNC: f[Q][NT], then FP32 g[Q][NT] (or the FP32 rest channel [NT] and
+    // the FP16 moving channels [Q-1][NT]); D3Q27: from the first 128-byte
+    // boundary of the dynamic area (tensor-copy destinations)
+    extern __shared__ __align__(16) float stage_raw[];
+    float *const stage = D == 3 ? stage_raw + (((128u - (smem_u32(stage_raw) & 127u)) & 127u) >> 2) : stage_raw;
+    // ASYNC with tensor maps: the copies' completion barrier
+    __shared__ unsigned long long tma_bar;
+    // tensor copies need the staging area 128-byte aligned (checked, uniform per CTA)
+    const bool use_tma = ASYNC && tm != nullptr && tm[0] != nullptr && (smem_u32(stage) & 127u) == 0;
 
     // Region slots are filled for coordinates below n + 2 (n + 1 for the flags)
     // along each axis: the tile's nodes use no farther neighbours, and
@@ -541,7 +606,23 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         }
         // the node's own populations for stage C, requested after the loads stage A
         // waits on (they would queue ahead of them otherwise)
-        if (ASYNC) {
+        if (use_tma) {
+            // one thread: a box of TX x TY x TZ nodes x all directions per array
+            // (x0 is a multiple of 8 nodes: 16-byte aligned inner coordinate)
+            if (tid == 0) {
+                mbar_init(&tma_bar, 1);
+                const unsigned bytes = (unsigned)(Q * NT * 4) +
+                                       (sizeof(GT) == 4 ? (unsigned)(Q * NT * 4) : (unsigned)(NT * 4 + (Q - 1) * NT * 2));
+                mbar_expect_tx(&tma_bar, bytes);
+                tma_load_4d(&stage[0], tm[0], x0, y0, z0, 0, &tma_bar);
+                if (sizeof(GT) == 4) {
+                    tma_load_4d(&stage[Q * NT], tm[1], x0, y0, z0, 0, &tma_bar);
+                } else {
+                    tma_load_3d(&stage[Q * NT], tm[1], x0, y0, z0, &tma_bar);
+                    tma_load_4d(&stage[(Q + 1) * NT], tm[2], x0, y0, z0, 0, &tma_bar);
+                }
+            }
+        } else if (ASYNC) {
             const int ax = x0 + tid % TX, ay = y0 + (tid / TX) % TY, az = z0 + tid / (TX * TY);
             if (ax < p.nx && ay < p.ny && az < p.nz) {
                 const long long an = (long long)ax + (long long)p.nx * ((long long)ay + (long long)p.ny * az);
@@ -629,8 +710,21 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     // every thread's staged copies complete before the barrier, so each thread
     // may read copies made by another (the FP16 pairs) and none is pending
     // when a thread leaves
-    if (ASYNC) cp_async_wait_all();
-    __syncthreads();
+    if (use_tma) {
+        // every thread waits on the copies' barrier (its completion makes the
+        // tensor copies visible to the waiting thread), at most one second; a
+        // CTA whose copies did not land flags the lattice, waits once more
+        // (bounded) so that no copy is left in flight, and skips the tile
+        bool lost = !mbar_wait_bounded(&tma_bar, 0, 1000000000ull);
+        if (__syncthreads_or(lost)) {
+            if (tid == 0) atomicOr(status, STATUS_TIMEOUT);
+            if (lost) mbar_wait_bounded(&tma_bar, 0, 1000000000ull);
+            return;
+        }
+    } else {
+        if (ASYNC) cp_async_wait_all();
+        __syncthreads();
+    }
 
     // Stage C: one node per thread
     const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
@@ -852,7 +946,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
     float al = 2.0f;
     if (bad) {
-        atomicOr(status, 1u);
+        atomicOr(status, STATUS_DIVERGED);
     } else if (xmax >= 1e-5f) {
         al = alpha_series<Q>(fp, dl);
         if (xmax > 0.07f) {
@@ -941,7 +1035,7 @@ __global__ void __launch_bounds__(256, MINB) step_batch_kernel(const BatchEntry 
     AuxOut none = {};
     // D2Q9 tiles sum their own moments; D3Q27 tiles read those of the moments kernel
     step_tile<D, GT, MODE_STEP, D == 3, D == 2>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type,
-                                                se.status, t.y, t.z, t.w, nullptr, none);
+                                                se.status, t.y, t.z, t.w, nullptr, none, se.tm);
 }
 
 // ---------------------------------------------------------------------------
