@@ -735,15 +735,20 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     const uint8_t tc = stype[sc];
     const long long n = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
     if (tc & TLB_SOLID) return;
-    // periodic neighbour coordinates, for the push-streaming store addresses
-    const int xm = x == 0 ? p.nx - 1 : x - 1, xq = x == p.nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? p.ny - 1 : y - 1, yq = y == p.ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? p.nz - 1 : z - 1, zq = z == p.nz - 1 ? 0 : z + 1;
+    // push-streaming store addresses: the node index plus one offset per axis
+    // and sign (periodic wrap included), formed once per node
+    const int oxm = x == 0 ? p.nx - 1 : -1, oxq = x == p.nx - 1 ? 1 - p.nx : 1;
+    const long long oym = (long long)(y == 0 ? p.ny - 1 : -1) * p.nx;
+    const long long oyq = (long long)(y == p.ny - 1 ? 1 - p.ny : 1) * p.nx;
+    const long long oz = D == 3 ? (long long)p.nx * p.ny : 0;
+    const long long ozm = D == 3 ? (z == 0 ? p.nz - 1 : -1) * oz : 0;
+    const long long ozq = D == 3 ? (z == p.nz - 1 ? 1 - p.nz : 1) * oz : 0;
     auto nbr = [&](int cx, int cy, int cz) -> long long {
-        int xx = cx == 0 ? x : (cx > 0 ? xq : xm);
-        int yy = cy == 0 ? y : (cy > 0 ? yq : ym);
-        int zz = cz == 0 ? z : (cz > 0 ? zq : zm);
-        return chk_node((long long)xx + (long long)p.nx * ((long long)yy + (long long)p.ny * zz), p);
+        long long m = n;
+        if (cx != 0) m += cx > 0 ? oxq : oxm;
+        if (cy != 0) m += cy > 0 ? oyq : oym;
+        if (D == 3 && cz != 0) m += cz > 0 ? ozq : ozm;
+        return chk_node(m, p);
     };
     const float r = srho[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
     const float ph = sphi[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
@@ -956,14 +961,24 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
     const float ab = al * p.beta;
 
+    // halfway bounce-back: bit i set when the neighbour x + c_i is solid (one
+    // mask for the f and g stores); D3Q27: only first-layer nodes have solid
+    // neighbours (the D2Q9 kernel, latency-bound, measured faster without
+    // that branch)
+    unsigned solid_nb = 0;
+    if (D == 2 || (tc & TLB_FIRST)) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
+            if (stype[m] & TLB_SOLID) solid_nb |= 1u << i;
+        }
+    }
+
     // f_new = f' + alpha beta D (Eq. ELBMequation); push streaming with halfway bounce-back
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float fn = (fp[i] - wt<D>(i)) + ab * (dl[i] * fp[i]);
-        int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
-        // D3Q27: only first-layer nodes have solid neighbours (the D2Q9 kernel,
-        // latency-bound, measured faster without this branch)
-        if ((D == 2 || (tc & TLB_FIRST)) && (stype[m] & TLB_SOLID))
+        if (solid_nb & (1u << i))
             f_out[(long long)opp<D>(i) * p.N + n] = fn;
         else
             f_out[(long long)i * p.N + nbr(cc<D>(i, 0), cc<D>(i, 1), cc<D>(i, 2))] = fn;
@@ -974,6 +989,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
 #pragma unroll
     for (int a = 0; a < D; ++a) v2 += v[a] * v[a];
     float gsum = 0.f, g0 = 0.f;
+    // g^eq_i = w_i (3 Gamma mu_phi + 3 phi c.v + 4.5 phi (c.v)^2 - 1.5 phi v^2), factored in c.v
+    const float gA = 3.0f * p.Gamma * mup - 1.5f * ph * v2, gB = 3.0f * ph, gC = 4.5f * ph;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float gi;
@@ -989,11 +1006,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         float cv = 0.f;
 #pragma unroll
         for (int a = 0; a < D; ++a) cv += (float)cc<D>(i, a) * v[a];
-        float ge = wt<D>(i) * (3.0f * p.Gamma * mup + 3.0f * ph * cv + 4.5f * ph * cv * cv - 1.5f * ph * v2);
+        float ge = wt<D>(i) * (gA + cv * (gB + gC * cv));
         gsum += ge;
         float gn = gi + (ge - gi) * p.inv_tau_g;
-        int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
-        if ((D == 2 || (tc & TLB_FIRST)) && (stype[m] & TLB_SOLID))
+        if (solid_nb & (1u << i))
             GIO<GT>::st(g_out, opp<D>(i), n, gn, p);
         else
             GIO<GT>::st(g_out, i, nbr(cc<D>(i, 0), cc<D>(i, 1), cc<D>(i, 2)), gn, p);
