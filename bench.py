@@ -302,6 +302,7 @@ def run_ours(args):
     if rank == 0 and not args.no_batch:
         result["batched"] = batched_sweep()
         result["served"] = served_mix()
+        result["tension_sweep"] = tension_sweep()
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
     if world > 1:
@@ -372,6 +373,26 @@ def batched_sweep(steps=10):
     for l in lats:
         l.close()
     return res
+
+
+def tension_sweep(grid=4, L=96, R=24.0, steps=3000):
+    """Surface-tension characterisation (Sec. III, Table 2): a grid x grid
+    map of subspace 6, three bubble lattices per point (one per interface
+    pair), all advanced by one batch; then gamma, Neumann angles and D_k per
+    point.  Reports the batch's stepping throughput and the whole sweep's
+    wall time (creation, stepping, measurement)."""
+    from paper_1904_06881_gb300 import tension as T
+
+    t0 = time.perf_counter()
+    res, t = T.sweep(T.grid(6, grid), L=L, R=R, steps=steps)
+    wall = time.perf_counter() - t0
+    ok = sum(1 for r in res if not r["failed"] and all(np.isfinite(r["theta"])))
+    return {"workload": "subspace 6 map, %d points x 3 bubbles (%d^2, R %.0f), %d steps" % (len(res), L, R, steps),
+            "lattices": t["lattices"], "nodes": t["nodes"], "batch_mlups": round(t["mlups"], 1),
+            "sweep_wall_s": round(wall, 3), "points_with_neumann_angles": ok,
+            "example": {"lam": res[0]["point"]["lam"], "kappa": res[0]["point"]["kappa"],
+                        "gamma": {k: round(v, 5) for k, v in res[0]["gamma"].items()},
+                        "theta_deg": [round(v, 2) for v in res[0]["theta"]]}}
 
 
 def served_mix(budget_gb=24.0, max_active=64, steps_per_round=100):

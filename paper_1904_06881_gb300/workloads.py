@@ -202,6 +202,21 @@ def big_periodic_drop_3d(n=256, R=None):
                 mask=np.zeros((n, n, n), np.uint8), rho=rho, phi=phi, steps=1000)
 
 
+def bubble_2d(pair, L, R, **params):
+    """Bubble test of Sec. III for one interface pair in a periodic L x L box:
+    a disc of radius R (tanh edge of width 4) at the box centre.  pair "12":
+    C2 (liquid 1) in C1 (gas); "13": C3 (liquid 2) in C1; "23": C3 in C2.
+    params override base_params (lam, kappa, ...)."""
+    y, x = np.mgrid[0:L, 0:L].astype(np.float64)
+    inside = _blob(np.hypot(x - L / 2.0, y - L / 2.0), R, 2.0)
+    zero = np.zeros_like(inside)
+    C2, C3 = {"12": (inside, zero), "13": (zero, inside), "23": (1.0 - inside, inside)}[pair]
+    p = base_params(**params)
+    rho, phi = phase_fields(C2, C3, rho_l=p["rho_l"], rho_g=p["rho_g"], chi=p["chi"])
+    return dict(name="bubble_%s_%d" % (pair, L), lattice=D2Q9, nx=L, ny=L, nz=1, params=p,
+                mask=np.zeros((1, L, L), np.uint8), rho=rho[None], phi=phi[None])
+
+
 def c4_requests(seed=4, n=64, rate=20.0):
     """Served mix: Poisson arrivals (mean `rate` per second) of requests drawn
     from sessile drops (64^2-256^2), capillary channels (256x64-1024x64) and
