@@ -217,6 +217,29 @@ def bubble_2d(pair, L, R, **params):
                 mask=np.zeros((1, L, L), np.uint8), rho=rho[None], phi=phi[None])
 
 
+def bislug_2d(H=19, L1=60, L2=60, gas=120, theta=60.0, x0=None, wetting=WET_GEOM_INTERP):
+    """Self-propelled bi-slug of Sec. VI: a periodic channel of height H
+    (solid rows y = 0 and y = H + 1, wall planes half a node inside) holding
+    a slug of C2 (length L1) followed along +x by a slug of C3 (length L2),
+    gas elsewhere (gas columns of total length `gas`); tanh edges of width 4.
+    Geometric wetting with theta_21 = theta_31 = theta_23 = theta."""
+    nx, ny = L1 + L2 + gas, H + 2
+    x0 = gas / 2.0 if x0 is None else x0
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    left = 0.5 * (1.0 + np.tanh((x - x0) / 2.0))
+    mid = 0.5 * (1.0 + np.tanh((x - x0 - L1) / 2.0))
+    right = 0.5 * (1.0 + np.tanh((x - x0 - L1 - L2) / 2.0))
+    C2, C3 = left - mid, mid - right
+    rho, phi = phase_fields(C2, C3)
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0, :] = 1
+    mask[ny - 1, :] = 1
+    params = base_params(wetting=wetting, theta_deg=(theta, theta, theta))
+    return dict(name="bislug_%dx%d" % (nx, ny), lattice=D2Q9, nx=nx, ny=ny, nz=1, params=params,
+                mask=mask[None], rho=rho[None], phi=phi[None], steps=20000,
+                slug=dict(H=H, L1=L1, L2=L2, gas=gas, x0=x0))
+
+
 def c4_requests(seed=4, n=64, rate=20.0):
     """Served mix: Poisson arrivals (mean `rate` per second) of requests drawn
     from sessile drops (64^2-256^2), capillary channels (256x64-1024x64) and
