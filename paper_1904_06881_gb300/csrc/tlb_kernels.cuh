@@ -189,11 +189,15 @@ __global__ void __launch_bounds__(256) moments_batch_kernel(const BatchEntry *__
     pdl_wait();
     int4 t = tiles[blockIdx.x];
     const BatchEntry &e = E[t.x];
-    constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
-    int lx = threadIdx.x % TX, ly = (threadIdx.x / TX) % TY, lz = threadIdx.x / (TX * TY);
-    int x = t.y + lx, y = t.z + ly, z = t.w + lz;
-    if (x >= e.p.nx || y >= e.p.ny || z >= e.p.nz) return;
-    long long n = (long long)x + (long long)e.p.nx * ((long long)y + (long long)e.p.ny * z);
+    // the moments need no neighbourhood: the k-th tile of a lattice (in the
+    // table's x-fastest order) takes its nodes k*NT .. k*NT + NT - 1 in
+    // memory order, so that a warp reads whole 128-byte lines; a lattice has
+    // at least N / NT tiles, so every node is covered once
+    constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z, NT = TX * TY * TZ;
+    const long long ntx = (e.p.nx + TX - 1) / TX, nty = (e.p.ny + TY - 1) / TY;
+    const long long k = t.y / TX + ntx * (t.z / TY + nty * (t.w / TZ));
+    const long long n = k * NT + threadIdx.x;
+    if (n >= e.p.N) return;
     moments_node<D, GT>(e.p, e.f_in, e.g_in, e.type, const_cast<float *>(e.rho), const_cast<float *>(e.phi), n);
 }
 
