@@ -151,8 +151,12 @@ int tlb_step(tlb_ctx *ctx, int nsteps);
  * in order is exactly one tlb_step.  A step is one launch (D2Q9) or two
  * (D3Q27).  Asynchronous. */
 int tlb_step_phase(tlb_ctx *ctx, int phase);
-/* Wait for the context stream and report TLB_E_DIVERGED if a kernel flagged
- * a non-positive density or population since the last check. */
+/* Wait for the context stream and report what the kernels flagged since the
+ * last check: TLB_E_TIMEOUT if a tile's tensor copies of its populations
+ * (D3Q27) did not complete within the kernel's one-second bound (the tile
+ * was skipped), else TLB_E_DIVERGED for a non-positive density or
+ * population; bounds-checked builds also report TLB_E_BOUNDS.  The error
+ * sticks to the context. */
 int tlb_sync(tlb_ctx *ctx);
 
 /* Fields of the current state (host FP64; any pointer may be NULL): rho,
