@@ -4,13 +4,18 @@ The library lands in paper_1904_06881_gb300/_build/libtlb.so.  Three
 translation units (host ABI, D2Q9 kernels, D3Q27 kernels) compile in
 parallel; only files newer than their object are rebuilt.
 
-build(check=True) makes the bounds-checked variant in _build_check/: every
-node index a kernel computes is tested against the lattice size, a bad one
-is recorded and its access skipped, and tlb_sync reports TLB_E_BOUNDS.  It
-is a test build (slower; the normal library is the product).  Load it with
-TLB_LIBRARY=<path> in the environment.
+Test builds (the normal library is the product), loaded with
+TLB_LIBRARY=<path> in the environment:
 
-    python -m paper_1904_06881_gb300.build [--force] [--check]
+  * build(check=True), in _build_check/: the bounds-checked variant: every
+    node index a kernel computes is tested against the lattice size, a bad
+    one is recorded and its access skipped, and tlb_sync reports
+    TLB_E_BOUNDS;
+  * build(timeout_test=True), in _build_timeout/: the D3Q27 step's tensor
+    copies are awaited for 16 bytes more than they send, so every such wait
+    runs out after its one-second bound and tlb_sync reports TLB_E_TIMEOUT.
+
+    python -m paper_1904_06881_gb300.build [--force] [--check | --timeout-test]
 """
 import os
 import subprocess
@@ -23,6 +28,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtlb.so")
 BUILD_CHECK = os.path.join(HERE, "_build_check")
 LIB_CHECK = os.path.join(BUILD_CHECK, "libtlb.so")
+BUILD_TIMEOUT = os.path.join(HERE, "_build_timeout")
+LIB_TIMEOUT = os.path.join(BUILD_TIMEOUT, "libtlb.so")
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--use_fast_math", "-diag-suppress", "177"]
@@ -41,9 +48,13 @@ def _newest(paths):
     return max(os.path.getmtime(p) for p in paths if os.path.exists(p))
 
 
-def build(verbose=False, force=False, check=False):
-    bdir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
-    extra = ["-DTLB_BOUNDS_CHECK"] if check else []
+def build(verbose=False, force=False, check=False, timeout_test=False):
+    if check:
+        bdir, lib, extra = BUILD_CHECK, LIB_CHECK, ["-DTLB_BOUNDS_CHECK"]
+    elif timeout_test:
+        bdir, lib, extra = BUILD_TIMEOUT, LIB_TIMEOUT, ["-DTLB_TEST_TMA_TIMEOUT"]
+    else:
+        bdir, lib, extra = BUILD, LIB, []
     os.makedirs(bdir, exist_ok=True)
     deps = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "tlb.h")]
     dep_time = _newest(deps)
@@ -71,4 +82,5 @@ def build(verbose=False, force=False, check=False):
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv, check="--check" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, check="--check" in sys.argv,
+                timeout_test="--timeout-test" in sys.argv))

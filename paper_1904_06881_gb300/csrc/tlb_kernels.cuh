@@ -617,7 +617,13 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                 mbar_init(&tma_bar, 1);
                 const unsigned bytes = (unsigned)(Q * NT * 4) +
                                        (sizeof(GT) == 4 ? (unsigned)(Q * NT * 4) : (unsigned)(NT * 4 + (Q - 1) * NT * 2));
+#ifdef TLB_TEST_TMA_TIMEOUT
+                // test builds only: the barrier expects 16 bytes more than the
+                // copies send, so its wait runs out and the timeout path runs
+                mbar_expect_tx(&tma_bar, bytes + 16u);
+#else
                 mbar_expect_tx(&tma_bar, bytes);
+#endif
                 tma_load_4d(&stage[0], tm[0], x0, y0, z0, 0, &tma_bar);
                 if (sizeof(GT) == 4) {
                     tma_load_4d(&stage[Q * NT], tm[1], x0, y0, z0, 0, &tma_bar);
