@@ -1,6 +1,6 @@
 """GPU (CUDA, sm_103a) vs FP64 oracle parity, through the C ABI.
 
-Tolerance (the benchmark spec): after 1000 steps in FP32 the densities and
+Tolerance (the project's parity bar): after 1000 steps in FP32 the densities and
 concentrations match the oracle within 1e-5, normwise: |rho_gpu - rho_ora| /
 (rho_l - rho_g), |phi_gpu - phi_ora| / chi and |C_gpu - C_ora| on every fluid
 node.  One-step comparisons from an identical state are held to FP32
