@@ -65,3 +65,24 @@ def test_invalid_arguments_rejected_on_host(L):
     with pytest.raises(tlb.TlbError) as e:
         tlb.tlb_create_ex(p)
     assert e.value.code == -4          # geometric angles limited to [20, 160] deg
+
+
+@pytest.mark.parametrize("variant", ["check", "timeout_test"])
+def test_test_builds_compile_and_export_the_same_symbols(variant):
+    """The bounds-checked and the timeout test builds (loaded by the GPU
+    tests through TLB_LIBRARY) compile here and export every declared entry
+    point; they report their own error codes by name."""
+    import subprocess
+    import sys
+
+    from paper_1904_06881_gb300 import build
+
+    path = build.build(**{variant: True})
+    code = ("import ctypes, sys; L = ctypes.CDLL(sys.argv[1]); names = sys.argv[2:]; "
+            "missing = [n for n in names if not hasattr(L, n)]; "
+            "L.tlb_strerror.restype = ctypes.c_char_p; "
+            "print(missing, L.tlb_strerror(-10).decode(), L.tlb_strerror(-7).decode())")
+    out = subprocess.run([sys.executable, "-c", code, path] + declared_entry_points(), capture_output=True,
+                         text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "[] index outside its array (bounds-checked build) device wait timed out", out.stdout
