@@ -164,9 +164,45 @@ def _sessile(wet, theta, kw=0.0, n=64, steps=6000):
     return _contact_angle(o.fields()["rho"][0], d["rho_l"], d["rho_g"])
 
 
+def _circle_fit_angle(rho, rl, rg, skip=3):
+    """Contact angle of a least-squares circle through the rho = (rho_l +
+    rho_g)/2 contour (linear interpolation along rows and columns, rows 1 +
+    skip and above), against the wall plane half a node above the solid row."""
+    half = 0.5 * (rl + rg)
+    ny, nx = rho.shape
+    pts = []
+    for y in range(1 + skip, ny - 2):
+        for x in range(nx):
+            a, b = rho[y, x], rho[y + 1, x]
+            if (a - half) * (b - half) < 0:
+                pts.append((x, y + (a - half) / (a - b)))
+            if x + 1 < nx:
+                c = rho[y, x + 1]
+                if (a - half) * (c - half) < 0:
+                    pts.append((x + (a - half) / (a - c), y))
+    p = np.array(pts)
+    A = np.column_stack([p[:, 0], p[:, 1], np.ones(len(p))])
+    k = np.linalg.lstsq(A, -(p[:, 0] ** 2 + p[:, 1] ** 2), rcond=None)[0]
+    xc, yc = -k[0] / 2, -k[1] / 2
+    R_ = np.sqrt(xc * xc + yc * yc - k[2])
+    return np.degrees(np.arccos((0.5 - yc) / R_))
+
+
 @pytest.mark.slow
-def test_neutral_wall_gives_ninety_degrees():
-    assert abs(_sessile(W.WET_FORCE, 90.0) - 90.0) < 3.0
+@pytest.mark.parametrize("wet", [W.WET_FORCE, W.WET_GEOM_EXTRAP, W.WET_GEOM_INTERP])
+def test_neutral_wall_gives_ninety_degrees(wet):
+    """A neutral wall (force method with kappa^w = 0; geometric schemes at
+    theta = 90 deg, whose ghost layer then mirrors the first fluid layer)
+    leaves the drop at 90 deg: 88.6 deg measured for every scheme at radius 16
+    (88.9 at radius 24: the gap closes with resolution)."""
+    n = 64
+    o = _mk(n, n, wetting=wet, theta_deg=(90.0, 90.0, 90.0))
+    mask, rho, phi = W.sessile_drop_2d(n, n, 16.0, xc=n / 2, yc=0.5)
+    o.set_solid(mask)
+    o.init_fields(rho, phi)
+    o.step(6000)
+    d = o.derived
+    assert abs(_circle_fit_angle(o.fields()["rho"][0], d["rho_l"], d["rho_g"]) - 90.0) < 2.0
 
 
 @pytest.mark.slow
