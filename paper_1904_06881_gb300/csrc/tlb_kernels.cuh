@@ -1289,24 +1289,26 @@ static void launch_step_batch(const BatchEntry *entries, const int4 *tiles, int 
 {
     constexpr int bytes = stage_bytes<D, GT>();
     constexpr int nt = Tile<D>::X * Tile<D>::Y * Tile<D>::Z;
-    static bool attr = false;   // the dynamic shared-memory opt-ins, once per process
-    static int nsm = 0;         // SMs of the device (D2Q9: the one-wave bound)
-    if constexpr (D == 2) {
-        if (!attr) {
-            cudaFuncSetAttribute(step_batch_kernel<D, GT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            cudaFuncSetAttribute(step_batch_kernel<D, GT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            attr = true;
+    // once per process, on the first launch (thread-safe static initialisation):
+    // the dynamic shared-memory opt-ins, and the SM count of the device that
+    // runs the library (D2Q9: the one-wave bound)
+    static const int nsm = [] {
+        constexpr int b = stage_bytes<D, GT>();
+        if constexpr (D == 2) {
+            cudaFuncSetAttribute(step_batch_kernel<D, GT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+            cudaFuncSetAttribute(step_batch_kernel<D, GT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        } else {
+            cudaFuncSetAttribute(step_batch_kernel<D, GT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
         }
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n;
+    }();
+    if constexpr (D == 2) {
         if (ntiles > 3 * nsm) launch_pdl(step_batch_kernel<D, GT, 4>, ntiles, nt, (size_t)bytes, st, entries, tiles);
         else launch_pdl(step_batch_kernel<D, GT, 3>, ntiles, nt, (size_t)bytes, st, entries, tiles);
     } else {
-        if (!attr) {
-            cudaFuncSetAttribute(step_batch_kernel<D, GT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            attr = true;
-        }
         launch_pdl(step_batch_kernel<D, GT, 2>, ntiles, nt, (size_t)bytes, st, entries, tiles);
     }
 }
