@@ -86,3 +86,17 @@ def test_test_builds_compile_and_export_the_same_symbols(variant):
                          text=True, timeout=120)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == "[] index outside its array (bounds-checked build) device wait timed out", out.stdout
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without the compiled library the binding raises on
+    first use (here: TLB_LIBRARY pointing at a file that does not exist)."""
+    import subprocess
+    import sys
+
+    code = ("from paper_1904_06881_gb300 import tlb\n"
+            "try:\n    tlb.Lattice(tlb.D2Q9, 16, 16, 1)\nexcept RuntimeError as e:\n    print('RAISED', e)\n")
+    env = dict(os.environ, TLB_LIBRARY=str(tmp_path / "absent" / "libtlb.so"))
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("RAISED libtlb.so not built"), out.stdout
