@@ -203,7 +203,10 @@ long long tlb_launch_count(const tlb_ctx *ctx);
  * word) is one static device array of TLB_NOALLOC_MAX_NODES * 13 + 256 bytes
  * (13.6 MB) that every GPU loading this library holds until exit.
  *   p          lattice, sizes and physics; at most TLB_NOALLOC_MAX_NODES
- *              (1048576) nodes, else TLB_E_INVAL; g_fp16 must be 0.
+ *              (1048576) nodes, else TLB_E_INVAL; g_fp16 must be 0.  Force
+ *              wetting given by angles takes its strengths from the
+ *              registered calibration tables, as tlb_create_ex does
+ *              (TLB_E_UNCALIBRATED without a matching table).
  *   mask       host, N bytes (1 = solid) or NULL for no walls.
  *   f, f_tmp   device, Q*N floats each: f holds the pre-collision populations
  *              minus the lattice weights (the layout tlb_get_populations

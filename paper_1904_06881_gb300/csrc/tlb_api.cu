@@ -1525,13 +1525,19 @@ std::mutex g_noalloc_mu;
 NoallocDevice g_noalloc_dev[64];
 }  // namespace
 
-extern "C" int tlb_step_noalloc(const tlb_params *p, const uint8_t *mask, float *f, float *f_tmp, void *g,
+extern "C" int tlb_step_noalloc(const tlb_params *pin, const uint8_t *mask, float *f, float *f_tmp, void *g,
                                 void *g_tmp, int nsteps, void *cuda_stream)
 {
     NvtxRange range("tlb_step_noalloc");
-    if (!p || !f || !f_tmp || !g || !g_tmp) return fail(TLB_E_INVAL, "null argument");
+    if (!pin || !f || !f_tmp || !g || !g_tmp) return fail(TLB_E_INVAL, "null argument");
     if (nsteps < 0) return fail(TLB_E_INVAL, "nsteps < 0");
-    int rc = validate(*p);
+    // the same parameter handling as tlb_create_ex: force wetting given by
+    // angles takes its strengths from the registered calibration tables
+    tlb_params pc = *pin;
+    int rc = apply_force_calibration(pc);
+    if (rc) return rc;
+    const tlb_params *p = &pc;
+    rc = validate(*p);
     if (rc) return rc;
     if (p->g_fp16) return fail(TLB_E_UNSUPPORTED, "tlb_step_noalloc takes FP32 g only");
     long long N = (long long)p->nx * p->ny * p->nz;

@@ -1,10 +1,20 @@
-"""The allocation-free entry point tlb_step_noalloc, for callers that cannot
-allocate device memory while they run, gives the same populations as the
-regular context API (tlb_step) on two calls in a row.
+"""The allocation-free entry point tlb_step_noalloc gives the same populations
+as the regular context API (tlb_step) on two calls in a row.
+
+tlb_step_noalloc serves callers that cannot allocate device memory while they
+run (a fixed device-memory budget carved up in advance, a framework's memory
+pool that a raw cudaMalloc would bypass, a loop that cannot take the
+synchronisation an allocation may imply); its scratch is a static device
+array inside the library.  The cases cover geometric wetting (D2Q9 channel),
+force wetting given by contact angles only, whose strengths come from the
+registered calibration tables exactly as for a context, and a small D3Q27
+lattice.
 
 This file is named to be collected last, so that a run stopping at the first
 failure has run every other test before it.
 """
+import json
+
 import numpy as np
 import pytest
 
@@ -13,12 +23,11 @@ from paper_1904_06881_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_step_noalloc_matches_context_steps():
+def _compare(wl, nsteps):
     import torch
 
     from paper_1904_06881_gb300 import tlb
 
-    wl = W.c1_capillary(wetting=W.WET_GEOM_INTERP)
     ref = tlb.lattice_from_workload(wl)
     c, w = tlb.tlb_lattice_directions(wl["lattice"])
     f0, g0 = ref.populations()                      # FP64, library direction order
@@ -28,18 +37,48 @@ def test_step_noalloc_matches_context_steps():
     f_tmp, g_tmp = torch.empty_like(f), torch.empty_like(g)
     p = tlb.make_params(wl["lattice"], wl["nx"], wl["ny"], wl["nz"], **wl["params"])
     stream = torch.cuda.current_stream().cuda_stream
+    fl = wl["mask"].reshape(-1) == 0
     for call in range(2):                           # two calls in a row: the scratch is reused
-        tlb.tlb_step_noalloc(p, wl["mask"], f.data_ptr(), f_tmp.data_ptr(), g.data_ptr(), g_tmp.data_ptr(), 7,
-                             stream)
-        ref.step(7)
+        tlb.tlb_step_noalloc(p, wl["mask"], f.data_ptr(), f_tmp.data_ptr(), g.data_ptr(), g_tmp.data_ptr(),
+                             nsteps, stream)
+        ref.step(nsteps)
         torch.cuda.synchronize()
         fr, gr = ref.populations()
         fn = f.double().cpu().numpy() + w[:, None]
         gn = g.double().cpu().numpy()
-        fl = wl["mask"].reshape(-1) == 0
-        # same kernels on the same inputs; the parity tests' one-step bound applies
+        # same arithmetic on the same inputs; the parity tests' one-step bound applies
         assert np.abs(fn[:, fl] - fr[:, fl]).max() <= 3e-6 * np.abs(fr[:, fl]).max(), call
         assert np.abs(gn[:, fl] - gr[:, fl]).max() <= 3e-6 * np.abs(gr[:, fl]).max(), call
+
+
+def test_step_noalloc_matches_context_steps():
+    _compare(W.c1_capillary(wetting=W.WET_GEOM_INTERP), 7)
+
+
+def _table_angle(lattice):
+    from paper_1904_06881_gb300 import tlb
+
+    with open(tlb.CALIBRATION_PATH) as fh:
+        tabs = [t for t in json.load(fh)["tables"] if t["lattice"] == lattice]
+    th = tabs[0]["theta_deg"]
+    return 0.5 * (th[0] + th[-1])                   # inside the calibrated range
+
+
+def test_step_noalloc_force_wetting_by_angles():
+    """Force wetting given by angles only (kappa^w = 0): both entry points map
+    the angles through the same calibration table."""
+    th = _table_angle(W.D2Q9)
+    mask, rho, phi = W.sessile_drop_2d(64, 48, 14.0, xc=30.3, yc=0.5)
+    wl = dict(lattice=W.D2Q9, nx=64, ny=48, nz=1, mask=mask, rho=rho, phi=phi,
+              params=W.base_params(wetting=W.WET_FORCE, theta_deg=(th, th, 90.0)))
+    _compare(wl, 5)
+
+
+def test_step_noalloc_d3q27():
+    th = _table_angle(W.D3Q27)
+    wl = W.c2_lubricated(nx=24, ny=20, nz=20, R=5.0, lub=3, gap=2)
+    wl["params"] = W.base_params(wetting=W.WET_FORCE, theta_deg=(90.0, th, 90.0))
+    _compare(wl, 3)
 
 
 def test_step_noalloc_rejects_oversize_lattice():
