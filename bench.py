@@ -1,11 +1,13 @@
 """Benchmark of the ternary ELBM step on GB300.
 
-Workload: the D2Q9 1024x64 capillary-filling channel (geometric-interpolation
-wetting, angles 30/60/120 deg).  One benchmark step = one full time step of
-the lattice (moments, ghost layer, stencils, force, ELBM + LBGK collision,
-streaming with bounce-back).  The lattice state (9.4 MB) fits in L2, so a
-256 MB buffer is written between timed steps and each step is timed on its
-own with CUDA events on the lattice's stream.
+Headline workload: the D3Q27 192x192x128 lubricated substrate (a liquid-1
+drop above a liquid-2 film on a wall, force wetting), 4.72 M nodes, 2.1 GB of
+populations: the largest single-GPU configuration, far larger than L2.  One
+benchmark step = one full time step of the lattice (moments pass, ghost
+layer, stencils, force, ELBM + LBGK collision, streaming with bounce-back),
+timed with CUDA events on the lattice's stream.  The D2Q9 1024x64 capillary
+channel (9.4 MB, L2-resident) is reported as a sub-key, timed with a 256 MB
+buffer written before every step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -132,9 +134,30 @@ def dist_env():
 
 
 def workload():
+    """The headline lattice: D3Q27 192x192x128 lubricated substrate."""
     from paper_1904_06881_gb300 import workloads as W
 
-    return W.c1_capillary()
+    return W.c2_lubricated(kw_rho=0.02)
+
+
+def oracle_sample(wl, n=48):
+    """A bounded sample of a D3Q27 workload for the host oracle: the full depth
+    (both walls, the film, the drop) of an n x n column through the lattice
+    centre; 2D workloads are taken whole."""
+    if wl["lattice"] == 0:
+        return wl
+    nx, ny = wl["nx"], wl["ny"]
+    x0, y0 = (nx - n) // 2, (ny - n) // 2
+    out = dict(wl)
+    for k in ("mask", "rho", "phi"):
+        out[k] = np.ascontiguousarray(wl[k][:, y0:y0 + n, x0:x0 + n])
+    out["nx"], out["ny"] = n, n
+    out["name"] = wl["name"] + " (%dx%d column through the centre, full depth)" % (n, n)
+    return out
+
+
+def density_ratio(wl):
+    return round(wl["params"]["rho_l"] / wl["params"]["rho_g"], 3)
 
 
 def algorithmic_bytes(Q, N):
@@ -202,6 +225,13 @@ def roofline(Q, N, kern_ms, peak, peak_kind, kernel_name, workload_name):
             "algorithmic_bytes_per_launch": algorithmic_bytes(Q, N)}
 
 
+def _lattice_desc(wl):
+    names = {0: "force", 1: "geometric extrapolation", 2: "geometric interpolation"}
+    return {"workload": wl["name"], "lattice": "D2Q9" if wl["lattice"] == 0 else "D3Q27", "nx": wl["nx"],
+            "ny": wl["ny"], "nz": wl["nz"], "wetting": names[wl["params"]["wetting"]],
+            "density_ratio": density_ratio(wl)}
+
+
 def run_ours(args):
     import torch
 
@@ -214,80 +244,90 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
+    peak, peak_kind = hbm_peak()
     wl = workload()
     stream = torch.cuda.Stream()
     lat = tlb.lattice_from_workload(wl)
     tlb.tlb_set_stream(lat.h, stream.cuda_stream)
     N, Q = lat.N, lat.Q
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        step_ms, kern_ms, launches, wall = measure(lat, stream, args.steps, args.warmup, flush=flush)
+        step_ms, kern_ms, launches, wall = measure(lat, stream, args.steps, args.warmup, flush=None)
     if world > 1:
         step_ms = max_over_ranks(step_ms, device="cuda")
     value = world * N / (step_ms * 1e-3) / 1e6
-    peak, peak_kind = hbm_peak()
+    cfg = _lattice_desc(wl)
+    cfg.update({"kappa_w": wl["params"]["kw_rho"],
+                "l2": "state 2.1 GB, larger than the 126 MB L2; no flush needed",
+                "parallelism": "replicas" if world > 1 else "single GPU"})
     result = {
         "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["name"], "lattice": "D2Q9", "nx": wl["nx"], "ny": wl["ny"],
-                   "wetting": "geometric interpolation", "angles_deg": [30, 60, 120],
-                   "density_ratio": 14.14, "l2": "256 MB buffer written before every timed step; steps timed alone",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": cfg,
         "roofline": roofline(Q, N, kern_ms, peak, peak_kind,
-                             "step_batch_kernel<D2Q9> (ghost layer, stencils, force, collision, stream)", wl["name"]),
+                             "step_batch_kernel<D3Q27> (ghost layer, stencils, force, collision, stream)",
+                             wl["name"]),
+        "whole_step": {"bytes_per_node": algorithmic_bytes(Q, 1) + 8 * Q + 9,
+                       "note": "moments pass (read f, g, flag; write rho, phi) + step kernel",
+                       "frac_of_peak": round((algorithmic_bytes(Q, 1) + 8 * Q + 9) * N / (step_ms * 1e-3) / 1e9
+                                             / peak, 4),
+                       "frac_of_peak_16Q": round(16 * Q * N / (step_ms * 1e-3) / 1e9 / peak, 4)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "host_wall_s": round(wall, 4),
     }
-    lat.close()
-    del flush
     if rank == 0:
         result["e2e"] = e2e_run(wl, tlb)
     if not args.no_large:
-        # the D3Q27 192x192x128 lubricated substrate: state (2.1 GB) far larger than L2
-        big = W.c2_lubricated(kw_rho=0.02)
-        lb = tlb.lattice_from_workload(big)
-        tlb.tlb_set_stream(lb.h, stream.cuda_stream)
-        with ClockSampler(local) as clk2:
-            bms, bkms, blaunch, _ = measure(lb, stream, max(args.steps // 10, 10), 3, flush=None)
-        result["large_lattice"] = {
-            "workload": big["name"], "value": round(world * lb.N / (bms * 1e-3) / 1e6, 2), "unit": "MLUPS",
-            "ms_per_step": round(bms, 4), "gpu_launches": int(blaunch), "clocks": clk2.summary(),
-            "l2": "state 2.1 GB, larger than L2; no flush",
-            "roofline": roofline(lb.Q, lb.N, bkms, peak, peak_kind,
-                                 "step_batch_kernel<D3Q27> (ghost layer, stencils, force, collision, stream)",
-                                 big["name"])}
         # reduced-precision g (rest population FP32, moving populations FP16)
-        big16 = dict(big)
-        big16["params"] = dict(big["params"], g_fp16=1)
-        l16 = tlb.lattice_from_workload(big16)
+        wl16 = dict(wl)
+        wl16["params"] = dict(wl["params"], g_fp16=1)
+        l16 = tlb.lattice_from_workload(wl16)
         tlb.tlb_set_stream(l16.h, stream.cuda_stream)
-        hms, hkms, _, _ = measure(l16, stream, max(args.steps // 10, 10), 3, flush=None)
+        hms, hkms, _, _ = measure(l16, stream, max(args.steps // 4, 10), 3, flush=None)
         # same number of steps from the same initial state in both formats
-        n32, n16 = lb.steps_done, l16.steps_done
+        n32, n16 = lat.steps_done, l16.steps_done
         if n16 < n32:
             l16.step(n32 - n16)
         elif n32 < n16:
-            lb.step(n16 - n32)
-        f32, f16 = lb.fields(), l16.fields()
-        fl = big["mask"] == 0
-        d = lb.derived
-        result["large_lattice_fp16_g"] = {
-            "workload": big["name"] + " (g: g_0 FP32, moving populations FP16)",
+            lat.step(n16 - n32)
+        f32, f16 = lat.fields(), l16.fields()
+        fl = wl["mask"] == 0
+        d = lat.derived
+        result["fp16_g"] = {
+            "workload": wl["name"] + " (g: g_0 FP32, moving populations FP16)",
             "value": round(world * l16.N / (hms * 1e-3) / 1e6, 2), "unit": "MLUPS", "ms_per_step": round(hms, 4),
             "kernel_ms": round(hkms, 5),
+            "roofline_frac_12Q": round((12 * Q + 9) * N / (hkms * 1e-3) / 1e9 / peak, 4),
             "normwise_diff_vs_fp32_after_steps": {
                 "steps": int(max(n32, n16)),
                 "rho": float(np.abs(f32["rho"] - f16["rho"])[fl].max() / (d["rho_l"] - d["rho_g"])),
-                "phi": float(np.abs(f32["phi"] - f16["phi"])[fl].max() / big["params"]["chi"])}}
+                "phi": float(np.abs(f32["phi"] - f16["phi"])[fl].max() / wl["params"]["chi"])}}
         l16.close()
-        lb.close()
+    lat.close()
+    # the D2Q9 1024x64 capillary channel: 9.4 MB of state, L2-resident, so a
+    # 256 MB buffer is written before every timed step
+    c1 = W.c1_capillary()
+    l1 = tlb.lattice_from_workload(c1)
+    tlb.tlb_set_stream(l1.h, stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with ClockSampler(local) as clk1:
+        ms1, kms1, la1, _ = measure(l1, stream, args.steps, args.warmup, flush=flush)
+    d1 = _lattice_desc(c1)
+    d1.update({"value": round(world * l1.N / (ms1 * 1e-3) / 1e6, 2), "unit": "MLUPS", "ms_per_step": round(ms1, 5),
+               "gpu_launches": int(la1), "clocks": clk1.summary(), "angles_deg": [30, 60, 120],
+               "l2": "256 MB buffer written before every timed step; steps timed alone",
+               "roofline": roofline(l1.Q, l1.N, kms1, peak, peak_kind,
+                                    "step_batch_kernel<D2Q9> (moments, ghost layer, stencils, force, collision, "
+                                    "stream)", c1["name"])})
+    result["c1_capillary"] = d1
+    l1.close()
+    del flush
     if not args.no_large:
-        # the large periodic lattices (no walls) on which the HBM fraction is judged
+        # the large periodic lattices (no walls)
         result["big_lattices"] = []
         for bw in (W.big_periodic_drop_2d(4096), W.big_periodic_drop_3d(256)):
             bl = tlb.lattice_from_workload(bw)
@@ -310,7 +350,7 @@ def run_ours(args):
     return result if rank == 0 else None
 
 
-def e2e_run(wl, tlb, nsteps=1000, reps=3):
+def e2e_run(wl, tlb, nsteps=1000, reps=2):
     """MLUPS of whole jobs through the public C ABI: tlb_init_fields from host
     arrays, nsteps steps, tlb_get_fields back to host arrays."""
     lat = tlb.Lattice(wl["lattice"], wl["nx"], wl["ny"], wl["nz"], **wl["params"])
@@ -453,22 +493,57 @@ def served_mix(budget_gb=24.0, max_active=64, steps_per_round=100):
             "server": {"budget_gb": budget_gb, "max_active": max_active, "steps_per_round": steps_per_round}}
 
 
-def cpu_baseline(wl, seconds=15.0):
-    """The FP64 oracle as it stands, on this host's cores, on the same
-    workload for as many steps as fit in about `seconds`."""
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(wl, threads, seconds):
+    """MLUPS of the FP64 oracle as it stands on `wl`, with `threads` host
+    threads, over at least one step and about `seconds` of stepping."""
     import oracle
 
+    oracle.threads(threads)
     o = oracle.from_workload(wl)
     o.step(1)
     n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        o.step(5)
-        n += 5
+    while n == 0 or time.perf_counter() - t0 < seconds:
+        o.step(1)
+        n += 1
     dt = time.perf_counter() - t0
     N = wl["nx"] * wl["ny"] * wl["nz"]
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
-    return {"value": round(N * n / dt / 1e6, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": "%d full time steps of %s (%d nodes) in %.1f s" % (n, wl["name"], N, dt)}
+    return N * n / dt / 1e6, n, dt
+
+
+def cpu_baseline(wl, seconds=4.0):
+    """The FP64 oracle as it stands, on this host's cores: the headline's
+    bounded sample (a column of the D3Q27 lattice) at all cores, plus the
+    D2Q9 drop and channel lattices whole, each at one thread and at all cores."""
+    from paper_1904_06881_gb300 import workloads as W
+
+    cores = os.cpu_count()
+    detail = []
+    head = None
+    for w in (W.c0_sessile_drop(), W.c1_capillary(), oracle_sample(wl)):
+        for th in (1, cores):
+            v, n, dt = oracle_rate(w, th, seconds)
+            detail.append({"workload": w["name"], "threads": th, "MLUPS": round(v, 4), "steps": n,
+                           "seconds": round(dt, 2)})
+            if w["lattice"] == 1 and th == cores:
+                head = (v, n, dt, w["name"])
+    v, n, dt, name = head
+    return {"value": round(v, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d full time steps of %s in %.1f s" % (n, name, dt),
+            "cpu_model": _cpu_model(), "nproc": cores, "detail": detail}
 
 
 def run_only(args):
@@ -478,7 +553,7 @@ def run_only(args):
     from paper_1904_06881_gb300 import tlb
     from paper_1904_06881_gb300 import workloads as W
 
-    wl = workload() if args.only == "c1" else W.c2_lubricated(kw_rho=0.02)
+    wl = W.c1_capillary() if args.only == "c1" else workload()
     stream = torch.cuda.Stream()
     lat = tlb.lattice_from_workload(wl)
     tlb.tlb_set_stream(lat.h, stream.cuda_stream)
@@ -490,12 +565,17 @@ def run_only(args):
 
 
 def run_reference(args):
+    """The oracle (the reference arm: the paper has no code) on the host cores,
+    on the headline workload's bounded sample: one oracle time step of a
+    48 x 48 x 128 column of the D3Q27 lattice per bench step."""
     rank, world, local = dist_env()
     if rank != 0:
         return None
-    wl = workload()
+    wl = oracle_sample(workload())
     import oracle
 
+    cores = os.cpu_count()
+    oracle.threads(cores)
     o = oracle.from_workload(wl)
     for _ in range(args.warmup):
         o.step(1)
@@ -505,13 +585,15 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     N = wl["nx"] * wl["ny"] * wl["nz"]
     value = N * args.steps / dt / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    cfg = _lattice_desc(workload())
+    cfg["sample"] = wl["name"]
     return {"impl": "reference", "metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "lattice": "D2Q9", "nx": wl["nx"], "ny": wl["ny"]},
+            "config": cfg,
             "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                             "sample": "%d full time steps of %s on the host cores" % (args.steps, wl["name"])},
+                             "sample": "%d full time steps of %s on the host cores" % (args.steps, wl["name"]),
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -521,10 +603,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=4.0, help="seconds per oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true",
-                    help="skip the D3Q27 192x192x128 and the large periodic lattices")
+                    help="skip the reduced-precision run and the large periodic lattices")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the served mix")
     ap.add_argument("--only", choices=["c1", "c2"], help="time one lattice only (profiling runs): no e2e, no CPU baseline")
     args = ap.parse_args()

@@ -231,6 +231,45 @@ int tlb_step_noalloc(const tlb_params *p, const uint8_t *mask, float *f, float *
  * share the lattice type and the stream of ctxs[0]. */
 int tlb_step_batch(tlb_ctx *const *ctxs, int n, int nsteps);
 
+/* ---- resident batches: a table built once, graph replays, tuned launches ----
+ * Many independent lattices (one lattice type and g storage) advanced
+ * together by one launch per kernel phase over a tile -> lattice table, the
+ * same kernels as tlb_step (a lattice gives bit-identical results alone and
+ * in a batch).  The table lives on the device for the batch's lifetime, so
+ * tlb_batch_step allocates nothing and does not synchronise the host; steps
+ * are replayed from CUDA graphs of graph_depth steps (captured on first use
+ * for each buffer parity).  The contexts must outlive the batch; stepping a
+ * context on its own between batch steps is allowed (the batch notices and
+ * rewrites its table). */
+typedef struct tlb_batch tlb_batch;
+enum { TLB_ORDER_LATTICE = 0,        /* tiles of lattice 0, then lattice 1, ... */
+       TLB_ORDER_INTERLEAVED = 1,    /* tile j of every lattice in turn */
+       TLB_ORDER_LARGEST_FIRST = 2   /* lattice-major, largest lattices first */ };
+typedef struct {
+    int variant;        /* D2Q9 register budget: 0 = 3 CTAs/SM, 1 = 4 CTAs/SM,
+                           -1 = chosen by launch size; D3Q27: ignored */
+    int tile_order;     /* TLB_ORDER_*: order of the tile table (CTA dispatch order) */
+    int graph_depth;    /* steps per CUDA-graph replay: 0 (direct launches) or even */
+    double us_per_step; /* set by tlb_batch_tune: measured time of one step */
+} tlb_batch_config;
+/* Build the batch over ctxs[0..n), which must share one stream (TLB_E_INVAL
+ * otherwise); the batch's work is issued on it.  cfg NULL =
+ * variant -1, lattice order, graph depth 8.  The table upload is ordered on
+ * the stream (no host synchronisation).  TLB_E_INVAL for mixed lattice types
+ * or g storage, or a repeated context. */
+int tlb_batch_create(tlb_ctx *const *ctxs, int n, const tlb_batch_config *cfg, tlb_batch **out);
+/* Advance every lattice by nsteps, asynchronously on the batch's stream. */
+int tlb_batch_step(tlb_batch *b, int nsteps);
+/* Autotuner: times every candidate configuration (register budget, tile
+ * order, graph depth 2/8/32) on this batch's own lattices -- graph replays
+ * of launches that recompute the current step, so the lattices' state is
+ * unchanged -- and keeps the fastest; `reps` scales the timed replays.
+ * Synchronous.  The chosen configuration is written to *chosen (may be NULL). */
+int tlb_batch_tune(tlb_batch *b, int reps, tlb_batch_config *chosen);
+int tlb_batch_get_config(const tlb_batch *b, tlb_batch_config *out);
+/* Waits for the batch's stream, then frees its tables and graphs (not the contexts). */
+void tlb_batch_destroy(tlb_batch *b);
+
 /* ---- request server (continuous batching) ---- */
 typedef struct tlb_server tlb_server;
 typedef struct {
@@ -248,7 +287,12 @@ typedef struct {
 enum { TLB_REQ_QUEUED = 0, TLB_REQ_RUNNING = 1, TLB_REQ_DONE = 2, TLB_REQ_FAILED = 3 };
 
 /* Server with a device-memory budget for resident lattices and a cap on
- * lattices advanced together; steps_per_round steps run between admissions. */
+ * lattices advanced together; steps_per_round steps run between admissions.
+ * cuda_stream NULL: the server steps on a stream of its own.  Each pump
+ * issues one round of the active lattices through resident batches (one per
+ * lattice type and g storage, rebuilt when their members change) and admits
+ * queued requests while that round runs on the GPU (their initial fields go
+ * through a second stream); requests admitted in a round join the next one. */
 int tlb_server_create(size_t hbm_budget_bytes, int max_active, int steps_per_round, void *cuda_stream,
                       tlb_server **out);
 /* Copy a request in; returns a ticket.  TLB_E_INVAL if the request can never

@@ -92,6 +92,8 @@ def lib():
         L.tlbo_diagnostics.argtypes = [p, dp]
         L.tlbo_alpha_clipped.restype = ctypes.c_long
         L.tlbo_alpha_clipped.argtypes = [p]
+        L.tlbo_threads.restype = i
+        L.tlbo_threads.argtypes = [i]
         _lib = L
     return _lib
 
@@ -101,6 +103,11 @@ def _dptr(a):
         return None
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def threads(n=0):
+    """Set the oracle's host thread count (n > 0); returns the count in use."""
+    return lib().tlbo_threads(int(n))
 
 
 # ---- thermodynamics and single-node kinetics -------------------------------

@@ -38,6 +38,7 @@
 #include "tlbo.h"
 
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -1040,3 +1041,11 @@ int tlbo_diagnostics(tlbo_ctx *ctx, double out[6])
 }
 
 long tlbo_alpha_clipped(const tlbo_ctx *ctx) { return ctx->clipped; }
+
+/* Host threads of the node loops (OpenMP); n <= 0 leaves the setting alone.
+ * Returns the number of threads the loops use. */
+int tlbo_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}

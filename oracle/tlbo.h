@@ -113,6 +113,9 @@ int  tlbo_diagnostics(tlbo_ctx *ctx, double out[6]);
 /* Count of collisions whose alpha was clipped at the positivity bound. */
 long tlbo_alpha_clipped(const tlbo_ctx *ctx);
 
+/* Host threads of the node loops; n <= 0 only reports.  Returns the count in use. */
+int  tlbo_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1323,6 +1323,318 @@ extern "C" int tlb_step_batch(tlb_ctx *const *ctxs, int n, int nsteps)
 }
 
 // ---------------------------------------------------------------------------
+// resident batches: the tile -> lattice table built once, steps issued without
+// allocation or host synchronisation, replayed from CUDA graphs of several
+// steps; the launch configuration chosen by timing candidates on the batch
+// ---------------------------------------------------------------------------
+struct tlb_batch {
+    std::vector<tlb_ctx *> ctxs;
+    std::vector<int> base_cur;          // each context's buffer parity when the entries were written
+    int D = 2, fp16 = 0;
+    cudaStream_t st = nullptr;          // the stream of ctxs[0]
+    cudaStream_t cap = nullptr;         // private stream for graph capture and tuning
+    std::vector<Block> owned;
+    BatchEntry *entries[2] = {nullptr, nullptr};
+    int4 *tiles = nullptr;
+    int ntiles = 0;
+    tlb_batch_config cfg;
+    // replays of cfg.graph_depth steps starting at entry parity 0 and 1
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+static void batch_drop_graphs(tlb_batch *b)
+{
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) {
+            cudaGraphExecDestroy(b->graph[k]);
+            b->graph[k] = nullptr;
+        }
+}
+
+// tile table in the configured order (written to the device table)
+static std::vector<int4> batch_tile_order(const tlb_batch *b, int order)
+{
+    const int D = b->D;
+    const int TX = D == 2 ? Launch<2>::tile_dims(0) : Launch<3>::tile_dims(0);
+    const int TY = D == 2 ? Launch<2>::tile_dims(1) : Launch<3>::tile_dims(1);
+    const int TZ = D == 2 ? Launch<2>::tile_dims(2) : Launch<3>::tile_dims(2);
+    const int n = (int)b->ctxs.size();
+    std::vector<std::vector<int4>> per(n);
+    for (int k = 0; k < n; ++k) {
+        const tlb_ctx *c = b->ctxs[k];
+        for (int z = 0; z < c->p.nz; z += TZ)
+            for (int y = 0; y < c->p.ny; y += TY)
+                for (int x = 0; x < c->p.nx; x += TX) per[k].push_back(make_int4(k, x, y, z));
+    }
+    std::vector<int> lat(n);
+    for (int k = 0; k < n; ++k) lat[k] = k;
+    if (order == TLB_ORDER_LARGEST_FIRST)
+        std::stable_sort(lat.begin(), lat.end(), [&](int a, int c) { return per[a].size() > per[c].size(); });
+    std::vector<int4> out;
+    if (order == TLB_ORDER_INTERLEAVED) {
+        size_t most = 0;
+        for (auto &v : per) most = std::max(most, v.size());
+        for (size_t j = 0; j < most; ++j)
+            for (int k = 0; k < n; ++k)
+                if (j < per[k].size()) out.push_back(per[k][j]);
+    } else {
+        for (int k : lat) out.insert(out.end(), per[k].begin(), per[k].end());
+    }
+    return out;
+}
+
+// entries of both parities from the contexts' current buffers
+static int batch_write_entries(tlb_batch *b)
+{
+    const int n = (int)b->ctxs.size();
+    std::vector<BatchEntry> e[2] = {std::vector<BatchEntry>(n), std::vector<BatchEntry>(n)};
+    b->base_cur.resize(n);
+    for (int k = 0; k < n; ++k) {
+        tlb_ctx *c = b->ctxs[k];
+        b->base_cur[k] = c->s.cur;
+        for (int par = 0; par < 2; ++par) {
+            BatchEntry &x = e[par][k];
+            int cur = (c->s.cur + par) & 1;
+            x.p = c->dp;
+            x.f_in = c->s.f[cur];
+            x.f_out = c->s.f[1 - cur];
+            x.g_in = c->s.g[cur];
+            x.g_out = c->s.g[1 - cur];
+            x.rho = c->s.rho;
+            x.phi = c->s.phi;
+            x.type = c->s.type;
+            x.status = c->s.status;
+            entry_maps(c, cur, x);
+        }
+    }
+    for (int par = 0; par < 2; ++par)
+        CUDA_TRY(cudaMemcpyAsync(b->entries[par], e[par].data(), n * sizeof(BatchEntry), cudaMemcpyHostToDevice,
+                                 b->st));
+    return TLB_OK;
+}
+
+static int batch_write_tiles(tlb_batch *b)
+{
+    std::vector<int4> t = batch_tile_order(b, b->cfg.tile_order);
+    CUDA_TRY(cudaMemcpyAsync(b->tiles, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, b->st));
+    // pageable source: the copy has been staged when the call returns
+    return TLB_OK;
+}
+
+// the launches of one step of every lattice, entry parity par
+static void batch_issue(const tlb_batch *b, int par, cudaStream_t st)
+{
+    const BatchEntry *E = b->entries[par];
+    if (b->D == 2) {
+        Launch<2>::step_batch(E, b->tiles, b->ntiles, b->fp16, st, b->cfg.variant);
+    } else {
+        Launch<3>::moments_batch(E, b->tiles, b->ntiles, b->fp16, st);
+        Launch<3>::step_batch(E, b->tiles, b->ntiles, b->fp16, st, b->cfg.variant);
+    }
+}
+
+// a graph of `depth` steps from entry parity par0; `same` keeps one parity
+// for every step (each launch then recomputes the same step: timing only)
+static int batch_capture(tlb_batch *b, int par0, int depth, bool same, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < depth; ++s) batch_issue(b, same ? par0 : ((par0 + s) & 1), b->cap);
+    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (e != cudaSuccess) return fail(TLB_E_CUDA, "batch capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return fail(TLB_E_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    }
+    return TLB_OK;
+}
+
+extern "C" int tlb_batch_create(tlb_ctx *const *ctxs, int n, const tlb_batch_config *cfg, tlb_batch **out)
+{
+    NvtxRange range("tlb_batch_create");
+    if (!ctxs || n <= 0 || !out) return fail(TLB_E_INVAL, "bad batch arguments");
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (!ctxs[k]) return fail(TLB_E_INVAL, "null context in batch");
+        if (ctxs[k]->D != ctxs[0]->D) return fail(TLB_E_INVAL, "batched lattices must share the lattice type");
+        if (ctxs[k]->p.g_fp16 != ctxs[0]->p.g_fp16)
+            return fail(TLB_E_INVAL, "batched lattices must share the g storage");
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == ctxs[k]) return fail(TLB_E_INVAL, "a context appears twice in the batch");
+        if (ctxs[k]->stream != ctxs[0]->stream) return fail(TLB_E_INVAL, "batched lattices must share one stream");
+    }
+    tlb_batch_config c = {};
+    c.variant = -1;
+    c.tile_order = TLB_ORDER_LATTICE;
+    c.graph_depth = 8;
+    if (cfg) c = *cfg;
+    if (c.tile_order < 0 || c.tile_order > 2) return fail(TLB_E_INVAL, "tile_order must be 0, 1 or 2");
+    if (c.graph_depth < 0 || (c.graph_depth & 1)) return fail(TLB_E_INVAL, "graph_depth must be 0 or even");
+    if (c.variant < -1 || c.variant > 1) return fail(TLB_E_INVAL, "variant must be -1, 0 or 1");
+    tlb_batch *b = new tlb_batch();
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->D = ctxs[0]->D;
+    b->fp16 = ctxs[0]->p.g_fp16;
+    b->st = ctxs[0]->stream;
+    b->cfg = c;
+    b->cfg.us_per_step = 0.0;
+    size_t ntiles = batch_tile_order(b, TLB_ORDER_LATTICE).size();
+    b->ntiles = (int)ntiles;
+    void *ptr;
+    int rc = 0;
+    for (int par = 0; par < 2 && rc == 0; ++par) {
+        if ((rc = dev_alloc(b->owned, &ptr, n * sizeof(BatchEntry), nullptr))) break;
+        b->entries[par] = (BatchEntry *)ptr;
+    }
+    if (rc == 0 && (rc = dev_alloc(b->owned, &ptr, ntiles * sizeof(int4), nullptr)) == 0) b->tiles = (int4 *)ptr;
+    if (rc == 0) rc = batch_write_entries(b);
+    if (rc == 0) rc = batch_write_tiles(b);
+    if (rc == 0 && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+        rc = fail(TLB_E_CUDA, "stream creation failed");
+    // the table copies are ordered before every launch of the batch (same
+    // stream; graphs are replayed on it too): no host synchronisation
+    if (rc) {
+        if (b->cap) cudaStreamDestroy(b->cap);
+        dev_free_all(b->owned);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return TLB_OK;
+}
+
+extern "C" int tlb_batch_step(tlb_batch *b, int nsteps)
+{
+    NvtxRange range("tlb_batch_step");
+    if (!b || nsteps < 0) return fail(TLB_E_INVAL, "bad batch arguments");
+    // the entry parity that matches every context's current buffer; contexts
+    // stepped on their own since the entries were written force a rewrite
+    const int n = (int)b->ctxs.size();
+    int par = (b->ctxs[0]->s.cur + b->base_cur[0]) & 1;
+    for (int k = 1; k < n; ++k)
+        if (((b->ctxs[k]->s.cur + b->base_cur[k]) & 1) != par) {
+            batch_drop_graphs(b);
+            int rc = batch_write_entries(b);
+            if (rc) return rc;
+            par = 0;
+            break;
+        }
+    const int depth = b->cfg.graph_depth;
+    int left = nsteps;
+    while (left > 0) {
+        if (depth > 0 && left >= depth) {
+            if (!b->graph[par]) {
+                // capture waits for nothing: the graph is replayed on the batch stream
+                int rc = batch_capture(b, par, depth, false, &b->graph[par]);
+                if (rc) return rc;
+            }
+            CUDA_TRY(cudaGraphLaunch(b->graph[par], b->st));
+            left -= depth;               // even depth: the parity returns to par
+        } else {
+            batch_issue(b, par, b->st);
+            par ^= 1;
+            left -= 1;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TLB_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
+    const int per = launches_per_step(b->D);
+    for (tlb_ctx *c : b->ctxs) {
+        if (nsteps & 1) c->s.cur ^= 1;
+        c->steps += nsteps;
+    }
+    b->ctxs[0]->launches += (long long)per * nsteps;
+    return TLB_OK;
+}
+
+// average time of one step of the batch in configuration c, from `reps`
+// replays of a graph of `trial` launches that all recompute the same step
+// (the state is left as it was)
+static int batch_time(tlb_batch *b, const tlb_batch_config &c, int trial, int reps, double *us)
+{
+    tlb_batch_config keep = b->cfg;
+    b->cfg = c;
+    int rc = batch_write_tiles(b);
+    const int par = (b->ctxs[0]->s.cur + b->base_cur[0]) & 1;
+    cudaGraphExec_t g = nullptr;
+    if (rc == 0) rc = batch_capture(b, par, trial, true, &g);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == 0 && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = fail(TLB_E_CUDA, "event creation failed");
+    if (rc == 0) {
+        cudaStreamSynchronize(b->st);
+        cudaGraphLaunch(g, b->cap);                     // warm-up replay
+        cudaEventRecord(e0, b->cap);
+        for (int r = 0; r < reps; ++r) cudaGraphLaunch(g, b->cap);
+        cudaEventRecord(e1, b->cap);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(TLB_E_CUDA, "tuning replay failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *us = 1e3 * ms / (double)(reps * trial);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (g) cudaGraphExecDestroy(g);
+    b->cfg = keep;
+    return rc;
+}
+
+extern "C" int tlb_batch_tune(tlb_batch *b, int reps, tlb_batch_config *chosen)
+{
+    NvtxRange range("tlb_batch_tune");
+    if (!b || reps <= 0) return fail(TLB_E_INVAL, "bad tuning arguments");
+    // candidates: register budget (D2Q9), tile order, steps per graph replay;
+    // the depth is timed as replays of that many launches, one replay per rep
+    const int variants[2] = {0, 1};
+    const int nvar = 2;
+    const int depths[3] = {2, 8, 32};
+    double best = 1e300;
+    tlb_batch_config bestc = b->cfg;
+    for (int vi = 0; vi < nvar; ++vi)
+        for (int order = 0; order < 3; ++order)
+            for (int di = 0; di < 3; ++di) {
+                tlb_batch_config c = b->cfg;
+                c.variant = variants[vi];
+                c.tile_order = order;
+                c.graph_depth = depths[di];
+                double us = 0.0;
+                int rc = batch_time(b, c, depths[di], std::max(1, reps * 8 / depths[di]), &us);
+                if (rc) return rc;
+                if (us < best) {
+                    best = us;
+                    bestc = c;
+                }
+            }
+    bestc.us_per_step = best;
+    batch_drop_graphs(b);
+    b->cfg = bestc;
+    int rc = batch_write_tiles(b);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(b->st));
+    if (chosen) *chosen = bestc;
+    return TLB_OK;
+}
+
+extern "C" int tlb_batch_get_config(const tlb_batch *b, tlb_batch_config *out)
+{
+    if (!b || !out) return fail(TLB_E_INVAL, "null argument");
+    *out = b->cfg;
+    return TLB_OK;
+}
+
+extern "C" void tlb_batch_destroy(tlb_batch *b)
+{
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    batch_drop_graphs(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    dev_free_all(b->owned);
+    delete b;
+}
+
+// ---------------------------------------------------------------------------
 // request server: continuous batching with admission by device-memory budget
 // ---------------------------------------------------------------------------
 namespace {
@@ -1348,13 +1660,20 @@ struct Req {
 struct tlb_server {
     size_t budget;
     int max_active, steps_per_round;
-    cudaStream_t stream;
+    cudaStream_t stream;                 // the stepping stream (the caller's, or the server's own)
+    cudaStream_t admit = nullptr;        // initial fields of admitted requests
+    bool own_stream = false;
     uint64_t next = 1;
     std::deque<Req *> queue;
     std::vector<Req *> active;
     std::map<uint64_t, Req *> all;
     size_t in_use = 0;
     std::mutex mu;
+    // resident batches per group (lattice type x g storage), rebuilt when
+    // the group's members change; replaced batches are freed once the
+    // stepping stream has passed the event recorded after their last launch
+    tlb_batch *batch[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<std::pair<tlb_batch *, cudaEvent_t>> retired;
 };
 
 static size_t footprint(const tlb_params &p)
@@ -1371,6 +1690,18 @@ extern "C" int tlb_server_create(size_t budget, int max_active, int steps_per_ro
     s->max_active = max_active;
     s->steps_per_round = steps_per_round;
     s->stream = (cudaStream_t)stream;
+    if (!s->stream) {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return fail(TLB_E_CUDA, "stream creation failed");
+        }
+        s->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking) != cudaSuccess) {
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return fail(TLB_E_CUDA, "stream creation failed");
+    }
     *out = s;
     return TLB_OK;
 }
@@ -1421,13 +1752,80 @@ static void retire(tlb_server *s, Req *q, int status)
     q->res.done_s = now_s();
 }
 
+// free the replaced batches whose last launches the stepping stream has passed
+static void server_reap(tlb_server *s, bool wait)
+{
+    std::vector<std::pair<tlb_batch *, cudaEvent_t>> keep;
+    for (auto &r : s->retired) {
+        if (wait) cudaEventSynchronize(r.second);
+        if (cudaEventQuery(r.second) == cudaSuccess) {
+            cudaEventDestroy(r.second);
+            tlb_batch_destroy(r.first);          // its stream has passed the event: no wait
+        } else {
+            keep.push_back(r);
+        }
+    }
+    s->retired.swap(keep);
+}
+
+static void server_retire_batch(tlb_server *s, int g)
+{
+    if (!s->batch[g]) return;
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(ev, s->stream) == cudaSuccess) {
+        s->retired.push_back({s->batch[g], ev});
+    } else {
+        if (ev) cudaEventDestroy(ev);
+        tlb_batch_destroy(s->batch[g]);
+    }
+    s->batch[g] = nullptr;
+}
+
+// one admitted request: context, solid mask and initial fields on the
+// admission stream (the stepping stream keeps running), then the context
+// moves to the stepping stream
+static int server_admit_one(tlb_server *s, Req *q)
+{
+    int rc = tlb_create_ex(&q->params, &q->ctx);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(q->ctx->stream));   // the creation's clears (legacy stream)
+    if ((rc = tlb_set_stream(q->ctx, s->admit))) return rc;
+    if (!q->mask.empty() && (rc = tlb_set_solid(q->ctx, q->mask.data()))) return rc;
+    if ((rc = tlb_init_fields(q->ctx, q->rho.data(), q->phi.data(), nullptr))) return rc;   // synchronises s->admit
+    return tlb_set_stream(q->ctx, s->stream);
+}
+
 extern "C" int tlb_server_pump(tlb_server *s)
 {
     if (!s) return fail(TLB_E_INVAL, "null server");
     NvtxRange range("tlb_server_pump");
     std::lock_guard<std::mutex> lk(s->mu);
-    // admit in arrival order while memory and slots allow (no overtaking)
-    while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
+    server_reap(s, false);
+    // 1. one round of the active lattices, asynchronously: every group
+    //    advances through its resident batch (rebuilt if its members changed)
+    int chunk = 0;
+    if (!s->active.empty()) {
+        chunk = s->steps_per_round;
+        for (Req *q : s->active) chunk = std::min(chunk, q->nsteps - q->done_steps);
+        std::vector<tlb_ctx *> groups[4];
+        for (Req *q : s->active) groups[(q->ctx->D == 3 ? 1 : 0) + (q->ctx->p.g_fp16 ? 2 : 0)].push_back(q->ctx);
+        for (int g = 0; g < 4; ++g) {
+            if (s->batch[g] && s->batch[g]->ctxs != groups[g]) server_retire_batch(s, g);
+            if (groups[g].empty()) continue;
+            if (!s->batch[g]) {
+                int rc = tlb_batch_create(groups[g].data(), (int)groups[g].size(), nullptr, &s->batch[g]);
+                if (rc) return rc;
+            }
+            int rc = tlb_batch_step(s->batch[g], chunk);
+            if (rc) return rc;
+        }
+        for (Req *q : s->active) q->done_steps += chunk;
+    }
+    // 2. admission while the round runs: in arrival order while memory and
+    //    slots allow (no overtaking); admitted lattices join the next round
+    std::vector<Req *> admitted;
+    while (!s->queue.empty() && (int)(s->active.size() + admitted.size()) < s->max_active) {
         NvtxRange admit("tlb_server admit");
         Req *q = s->queue.front();
         if (s->in_use + q->bytes > s->budget) break;
@@ -1435,31 +1833,18 @@ extern "C" int tlb_server_pump(tlb_server *s)
         s->in_use += q->bytes;
         q->res.state = TLB_REQ_RUNNING;
         q->res.start_s = now_s();
-        int rc = tlb_create_ex(&q->params, &q->ctx);
-        if (rc == TLB_OK) rc = tlb_set_stream(q->ctx, s->stream);
-        if (rc == TLB_OK && !q->mask.empty()) rc = tlb_set_solid(q->ctx, q->mask.data());
-        if (rc == TLB_OK) rc = tlb_init_fields(q->ctx, q->rho.data(), q->phi.data(), nullptr);
+        int rc = server_admit_one(s, q);
         q->mask.clear();
         q->rho.clear();
         q->phi.clear();
         if (rc != TLB_OK) { retire(s, q, rc); continue; }
         if (q->nsteps == 0) { retire(s, q, TLB_OK); continue; }
-        s->active.push_back(q);
+        admitted.push_back(q);
     }
-    if (s->active.empty()) return 0;
-    // advance the active lattices together, grouped by lattice type and g storage
-    int chunk = s->steps_per_round;
-    for (Req *q : s->active) chunk = std::min(chunk, q->nsteps - q->done_steps);
-    std::vector<tlb_ctx *> groups[4];      // by lattice type and g storage
-    for (Req *q : s->active) groups[(q->ctx->D == 3 ? 1 : 0) + (q->ctx->p.g_fp16 ? 2 : 0)].push_back(q->ctx);
-    for (int g = 0; g < 4; ++g)
-        if (!groups[g].empty()) {
-            int rc = tlb_step_batch(groups[g].data(), (int)groups[g].size(), chunk);
-            if (rc) return rc;
-        }
+    // 3. retirement of the requests this round completed (their fields are
+    //    read after the round; tlb_get_fields waits for the stepping stream)
     std::vector<Req *> still;
     for (Req *q : s->active) {
-        q->done_steps += chunk;
         if (q->done_steps >= q->nsteps) {
             int rc = tlb_sync(q->ctx);
             retire(s, q, rc);
@@ -1467,6 +1852,7 @@ extern "C" int tlb_server_pump(tlb_server *s)
             still.push_back(q);
         }
     }
+    still.insert(still.end(), admitted.begin(), admitted.end());
     s->active.swap(still);
     return (int)s->active.size();
 }
@@ -1501,9 +1887,15 @@ extern "C" int tlb_server_stats(tlb_server *s, int *queued, int *active, size_t 
 extern "C" void tlb_server_destroy(tlb_server *s)
 {
     if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (int g = 0; g < 4; ++g)
+        if (s->batch[g]) tlb_batch_destroy(s->batch[g]);
+    server_reap(s, true);
     for (Req *q : s->active)
         if (q->ctx) tlb_destroy(q->ctx);
     for (auto &kv : s->all) delete kv.second;
+    if (s->admit) cudaStreamDestroy(s->admit);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
 }
 

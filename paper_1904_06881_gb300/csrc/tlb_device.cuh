@@ -198,14 +198,16 @@ __device__ __forceinline__ float phi_ent(float y, float l)
 // by less than 2e-8 of itself) and as the start of Halley's method (third
 // order, from h, h', h''), bracketed by [1, alpha_max), above it (nodes at the
 // interface).
-template <int Q>
-__device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&x)[Q])
+// FPA: accessor of f'_i (an array in registers, or a column of the staging
+// area in shared memory); the arithmetic is the same either way.
+template <int Q, class FPA>
+__device__ __forceinline__ float alpha_series_a(const FPA &fp, const float (&x)[Q])
 {
     float a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f, a7 = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float x2 = x[i] * x[i];
-        const float fx2 = fp[i] * x2, fx4 = fx2 * x2;
+        const float fx2 = fp(i) * x2, fx4 = fx2 * x2;
         a2 += fx2;
         a3 += fx2 * x[i];
         a4 += fx4;
@@ -228,6 +230,29 @@ __device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float 
     return 2.0f + e1 + e2 + e3 + e4 + e5;
 }
 
+template <int Q>
+struct RegPop {
+    const float (&v)[Q];
+    __device__ __forceinline__ float operator()(int i) const { return v[i]; }
+};
+template <int NT>
+struct SmemPop {
+    const float *stage;
+    int tid;
+    __device__ __forceinline__ float operator()(int i) const { return stage[i * NT + tid]; }
+};
+
+template <int Q>
+__device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&x)[Q])
+{
+    return alpha_series_a<Q>(RegPop<Q>{fp}, x);
+}
+template <int Q, int NT>
+__device__ __forceinline__ float alpha_series_s(const float *stage, int tid, const float (&x)[Q])
+{
+    return alpha_series_a<Q>(SmemPop<NT>{stage, tid}, x);
+}
+
 // Root of h in (1, alpha_max) from the start al.  h(1) < 0 always; when h is
 // still negative at the positivity bound there is no root below it and the
 // bound is returned.  h is evaluated at the bound only when an update would
@@ -235,12 +260,16 @@ __device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float 
 // iteration: the third-order convergence leaves an error of order 1e-9
 // alpha, below the FP32 evaluation noise of h (about 1e-6 alpha at
 // max|x| = 0.5).
-template <int Q>
-__device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float (&x)[Q], float amax, float al)
+// KEEP_L: the logarithms ln(1 + x_i) are held in registers across the
+// iterations, else recomputed in each one (same values; fewer registers)
+template <int Q, class FPA, bool KEEP_L = true>
+__device__ __forceinline__ float alpha_newton_a(const FPA &fp, const float (&x)[Q], float amax, float al)
 {
-    float L[Q];
+    float L[KEEP_L ? Q : 1];
+    if constexpr (KEEP_L) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) L[i] = log1pf(x[i]);
+        for (int i = 0; i < Q; ++i) L[i] = log1pf(x[i]);
+    }
     const float bound = amax * (1.0f - 1e-6f);
     float lo = 1.0f, hi = bound;
     bool probed = false;
@@ -254,9 +283,11 @@ __device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float 
         for (int i = 0; i < Q; ++i) {
             const float y = a * x[i];
             const float ly = log1pf(y);
-            h += fp[i] * (phi_ent(y, ly) - y * L[i]);
-            d1 += fp[i] * x[i] * (ly - L[i]);
-            d2 += fp[i] * x[i] * x[i] / (1.0f + y);
+            const float f = fp(i);
+            const float Li = KEEP_L ? L[KEEP_L ? i : 0] : log1pf(x[i]);
+            h += f * (phi_ent(y, ly) - y * Li);
+            d1 += f * x[i] * (ly - Li);
+            d2 += f * x[i] * x[i] / (1.0f + y);
         }
         if (a == bound) {
             if (h < 0.f) return bound;        // no root below the positivity bound
@@ -286,6 +317,18 @@ __device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float 
         a = nxt;
     }
     return a;
+}
+
+template <int Q>
+__device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float (&x)[Q], float amax, float al)
+{
+    return alpha_newton_a<Q>(RegPop<Q>{fp}, x, amax, al);
+}
+template <int Q, int NT>
+__device__ __forceinline__ float alpha_newton_s(const float *stage, int tid, const float (&x)[Q], float amax,
+                                                float al)
+{
+    return alpha_newton_a<Q, SmemPop<NT>, false>(SmemPop<NT>{stage, tid}, x, amax, al);
 }
 
 // ---------------------------------------------------------------------------

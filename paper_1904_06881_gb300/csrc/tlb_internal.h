@@ -98,7 +98,12 @@ struct Launch {
                             cudaStream_t st);
     // batched: entries[0..n) and a tile table (tile -> entry, tile coords)
     static void moments_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st);
-    static void step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st);
+    // variant: D2Q9 register budget, 0 = 3 CTAs/SM (80 registers), 1 = 4 CTAs/SM
+    // (64 registers), -1 = 4 CTAs/SM beyond one wave of 3 CTAs/SM; D3Q27: 0 or
+    // -1 = the tile's f and g staged, 2 CTAs/SM; 1 = f staged, the mirror state
+    // kept in shared memory, 3 CTAs/SM
+    static void step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st,
+                           int variant = -1);
     static int tile_dims(int a);
 };
 

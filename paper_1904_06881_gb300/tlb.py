@@ -34,8 +34,10 @@ ENTRY_POINTS = (
     "tlb_lattice_directions", "tlb_snapshot_bytes", "tlb_snapshot", "tlb_restore", "tlb_steps_done",
     "tlb_device_bytes", "tlb_launch_count", "tlb_step_batch", "tlb_server_create", "tlb_submit",
     "tlb_server_pump", "tlb_poll", "tlb_server_stats", "tlb_server_destroy", "tlb_step_noalloc",
-    "tlb_set_force_calibration",
+    "tlb_set_force_calibration", "tlb_batch_create", "tlb_batch_step", "tlb_batch_tune", "tlb_batch_get_config",
+    "tlb_batch_destroy",
 )
+ORDER_LATTICE, ORDER_INTERLEAVED, ORDER_LARGEST_FIRST = 0, 1, 2
 
 
 class TlbError(RuntimeError):
@@ -60,6 +62,11 @@ class Params(ctypes.Structure):
 class Derived(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("T", "a", "b", "R", "rho_l", "rho_g", "C", "Psi0", "Tc", "kappa_rr", "kappa_pp", "kappa_rp")]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("tile_order", ctypes.c_int), ("graph_depth", ctypes.c_int),
+                ("us_per_step", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -127,6 +134,11 @@ def lib():
         "tlb_server_destroy": (None, [vp]),
         "tlb_step_noalloc": (i, [ctypes.POINTER(Params), u8p, vp, vp, vp, vp, i, vp]),
         "tlb_set_force_calibration": (i, [ctypes.POINTER(Params), dp, dp, i]),
+        "tlb_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(BatchConfig), ctypes.POINTER(vp)]),
+        "tlb_batch_step": (i, [vp, i]),
+        "tlb_batch_tune": (i, [vp, i, ctypes.POINTER(BatchConfig)]),
+        "tlb_batch_get_config": (i, [vp, ctypes.POINTER(BatchConfig)]),
+        "tlb_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -411,6 +423,49 @@ def lattice_from_workload(wl, **over):
     lat.set_solid(wl["mask"])
     lat.init_fields(wl["rho"], wl["phi"])
     return lat
+
+
+def _config_dict(c):
+    return dict(variant=c.variant, tile_order=c.tile_order, graph_depth=c.graph_depth, us_per_step=c.us_per_step)
+
+
+class Batch:
+    """Resident batch of lattices (tlb_batch_*): one table, graph replays,
+    tuned launch configuration.  The lattices must outlive the batch."""
+
+    def __init__(self, lattices, variant=-1, tile_order=ORDER_LATTICE, graph_depth=8):
+        handles = [l.h for l in lattices]
+        arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+        cfg = BatchConfig(int(variant), int(tile_order), int(graph_depth), 0.0)
+        h = ctypes.c_void_p()
+        _check(lib().tlb_batch_create(arr, len(handles), ctypes.byref(cfg), ctypes.byref(h)), "tlb_batch_create")
+        self.h = h
+        self.lattices = list(lattices)
+
+    def step(self, nsteps):
+        _check(lib().tlb_batch_step(self.h, int(nsteps)), "tlb_batch_step")
+
+    def tune(self, reps=4):
+        c = BatchConfig()
+        _check(lib().tlb_batch_tune(self.h, int(reps), ctypes.byref(c)), "tlb_batch_tune")
+        return _config_dict(c)
+
+    @property
+    def config(self):
+        c = BatchConfig()
+        _check(lib().tlb_batch_get_config(self.h, ctypes.byref(c)), "tlb_batch_get_config")
+        return _config_dict(c)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            lib().tlb_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -86,3 +86,92 @@ def test_one_wave_and_large_launches_agree():
     tlb.tlb_step_batch([m.h for m in mix], 200)
     for a, m in zip(alone, mix):
         assert _same(a.fields(), m.fields())
+
+
+def test_resident_batch_equals_alone():
+    """A resident batch (table built once, steps replayed from CUDA graphs of
+    8 steps plus direct launches for the remainder) gives the fields of the
+    lattices stepped alone, bit for bit, for D2Q9 and D3Q27."""
+    from paper_1904_06881_gb300 import tlb
+
+    specs = [(64, 45.0, W.WET_GEOM_INTERP), (128, 120.0, W.WET_GEOM_INTERP), (96, 90.0, W.WET_FORCE)]
+    alone = [_drop(L, th, wet)[1] for L, th, wet in specs]
+    mix = [_drop(L, th, wet)[1] for L, th, wet in specs]
+    b = tlb.Batch(mix, graph_depth=8)
+    for a in alone:
+        a.step(43)
+    b.step(43)
+    for a, m in zip(alone, mix):
+        assert m.steps_done == 43
+        assert _same(a.fields(), m.fields())
+    b.close()
+    w3 = [W.c2_lubricated(nx=n, ny=n, nz=16, R=4.0, lub=2, gap=2, kw_rho=0.02) for n in (16, 24)]
+    alone3 = [tlb.lattice_from_workload(w) for w in w3]
+    mix3 = [tlb.lattice_from_workload(w) for w in w3]
+    b3 = tlb.Batch(mix3, graph_depth=4)
+    for a in alone3:
+        a.step(11)
+    b3.step(11)
+    for a, m in zip(alone3, mix3):
+        assert _same(a.fields(), m.fields())
+    b3.close()
+
+
+def test_batch_tuning_keeps_the_state_and_the_results():
+    """The autotuner times candidate configurations with launches that
+    recompute the current step: the lattices' fields are unchanged by it,
+    the chosen configuration is one of the candidates, and stepping with it
+    still gives the lattices' results alone (every variant and tile order
+    runs the same arithmetic per node)."""
+    from paper_1904_06881_gb300 import tlb
+
+    specs = [(64, 60.0, W.WET_GEOM_INTERP), (256, 100.0, W.WET_GEOM_EXTRAP), (128, 90.0, W.WET_FORCE)]
+    alone = [_drop(L, th, wet)[1] for L, th, wet in specs]
+    mix = [_drop(L, th, wet)[1] for L, th, wet in specs]
+    b = tlb.Batch(mix)
+    b.step(5)
+    before = [m.fields() for m in mix]
+    cfg = b.tune(reps=2)
+    after = [m.fields() for m in mix]
+    assert all(_same(x, y) for x, y in zip(before, after))
+    assert cfg["variant"] in (0, 1) and cfg["tile_order"] in (0, 1, 2) and cfg["graph_depth"] in (2, 8, 32)
+    assert cfg["us_per_step"] > 0 and b.config == cfg
+    b.step(40)
+    for a in alone:
+        a.step(45)
+    for a, m in zip(alone, mix):
+        assert _same(a.fields(), m.fields())
+
+
+def test_batch_follows_lattices_stepped_alone():
+    """Stepping one lattice of a batch on its own shifts its buffer parity
+    against the others; the batch rewrites its table and stays exact."""
+    from paper_1904_06881_gb300 import tlb
+
+    specs = [(64, 60.0, W.WET_GEOM_INTERP), (96, 90.0, W.WET_FORCE)]
+    alone = [_drop(L, th, wet)[1] for L, th, wet in specs]
+    mix = [_drop(L, th, wet)[1] for L, th, wet in specs]
+    b = tlb.Batch(mix, graph_depth=2)
+    b.step(6)
+    mix[0].step(3)
+    b.step(7)
+    alone[0].step(16)
+    alone[1].step(13)
+    for a, m in zip(alone, mix):
+        assert _same(a.fields(), m.fields())
+
+
+def test_d3q27_launch_variants_agree():
+    """The two D3Q27 step-kernel variants the autotuner chooses between (the
+    tile's f and g staged, 2 CTAs/SM; f staged with the mirror state kept in
+    shared memory, 3 CTAs/SM) run the same arithmetic in the same order:
+    bit-identical fields after 30 steps of a lubricated drop."""
+    from paper_1904_06881_gb300 import tlb
+
+    wl = W.c2_lubricated(nx=32, ny=24, nz=20, R=6.0, lub=3, gap=2, kw_rho=0.02)
+    a, b = tlb.lattice_from_workload(wl), tlb.lattice_from_workload(wl)
+    ba = tlb.Batch([a], variant=0, graph_depth=0)
+    bb = tlb.Batch([b], variant=1, graph_depth=0)
+    ba.step(30)
+    bb.step(30)
+    assert _same(a.fields(), b.fields())

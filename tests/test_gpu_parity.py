@@ -21,7 +21,7 @@ import pytest
 import oracle
 from paper_1904_06881_gb300 import workloads as W
 
-from helpers import gpu_from_workload, match_directions, normwise, oracle_from_workload
+from helpers import gpu_from_workload, match_directions, normwise, oracle_from_workload, pointwise_rho, record
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -129,7 +129,9 @@ def test_c0_1000_steps(wet, th):
     g, o = _pair(wl)
     g.step(1000)
     o.step(1000)
-    e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
+    fg, fo = g.fields(), o.fields()
+    e = normwise(fg, fo, o.derived, mask=wl["mask"])
+    record("c0 1000 steps, wetting %d" % wet, normwise=e, pointwise_rho=pointwise_rho(fg, fo, wl["mask"]), bound=TOL)
     assert e["rho"] <= TOL and e["phi"] <= TOL and e["C"] <= TOL, e
 
 
@@ -143,7 +145,10 @@ def test_amplifying_cases_1000_steps(case):
     g = gpu_from_workload(wl)
     g.step(1000)
     o, ref = _perturbed_oracle_spread(wl, 1000)
-    e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
+    fg, fo = g.fields(), o.fields()
+    e = normwise(fg, fo, o.derived, mask=wl["mask"])
+    record(case + ", 1000 steps", normwise=e, perturbed_oracle_spread=ref,
+           pointwise_rho=pointwise_rho(fg, fo, wl["mask"]), bound={k: max(TOL, 3 * ref[k]) for k in ref})
     for k in ("rho", "phi", "C"):
         assert e[k] <= max(TOL, 3 * ref[k]), (e, ref)
 
@@ -153,34 +158,44 @@ def test_d3q27_lubricated_small_1000_steps():
     g, o = _pair(wl)
     g.step(1000)
     o.step(1000)
-    e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
+    fg, fo = g.fields(), o.fields()
+    e = normwise(fg, fo, o.derived, mask=wl["mask"])
+    record("D3Q27 lubricated 32x32x20, 1000 steps", normwise=e, pointwise_rho=pointwise_rho(fg, fo, wl["mask"]),
+           bound=TOL)
     assert e["rho"] <= TOL and e["phi"] <= TOL and e["C"] <= TOL, e
 
 
+# Reduced-precision g storage (g_0 in FP32, the moving populations in FP16,
+# scaled): its error against the FP64 oracle is reported for every case and
+# bounded by FP16_TOL, the largest error measured on these cases (6e-6 after
+# 200 steps) with a margin of 3.
+FP16_TOL = 2e-5
+
+
 def test_d3q27_fp16_order_parameter_error_is_bounded():
-    """Reduced-precision g storage (g_0 in FP32, moving populations in FP16
-    scaled by 16) is not held to the FP32 bar; its error against the FP64
-    oracle after 200 steps is reported and bounded by 1e-3 (normwise), the
-    accumulation of the FP16 rounding (2^-11 relative) of the moving
-    populations."""
     wl = _small3d(g_fp16=1)
     g = gpu_from_workload(wl)
     o = oracle_from_workload(wl)
     g.step(200)
     o.step(200)
-    e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
-    print("FP16 g storage, 200 steps, normwise error vs FP64 oracle:", e)
-    assert e["phi"] < 1e-3 and e["rho"] < 1e-3 and e["C"] < 1e-3, e
+    fg, fo = g.fields(), o.fields()
+    e = normwise(fg, fo, o.derived, mask=wl["mask"])
+    record("D3Q27 FP16 g storage, 200 steps", normwise=e, pointwise_rho=pointwise_rho(fg, fo, wl["mask"]),
+           bound=FP16_TOL)
+    assert e["phi"] < FP16_TOL and e["rho"] < FP16_TOL and e["C"] < FP16_TOL, e
 
 
-def test_c2_full_size_first_steps_match():
-    """Full 192x192x128 D3Q27 lattice in the launch configuration of the
-    benchmark: the first two steps match the oracle on every fluid node."""
+def test_c2_full_size_100_steps():
+    """The full 192x192x128 D3Q27 lattice in the launch configuration of the
+    benchmark: after 100 steps every fluid node matches the oracle."""
     wl = W.c2_lubricated(kw_rho=0.02)
     g, o = _pair(wl)
-    g.step(2)
-    o.step(2)
-    e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
+    g.step(100)
+    o.step(100)
+    fg, fo = g.fields(), o.fields()
+    e = normwise(fg, fo, o.derived, mask=wl["mask"])
+    record("c2 192x192x128 full size, 100 steps", normwise=e, pointwise_rho=pointwise_rho(fg, fo, wl["mask"]),
+           bound=TOL)
     assert e["rho"] <= TOL and e["phi"] <= TOL and e["C"] <= TOL, e
 
 
@@ -257,6 +272,8 @@ def test_lattices_smaller_than_a_tile(lattice, nx, ny, nz, wet, R):
     g.step(100)
     o, ref = _perturbed_oracle_spread(wl, 100)
     e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
+    record("tiny %dx%dx%d wetting %d, 100 steps" % (nx, ny, nz, wet), normwise=e, perturbed_oracle_spread=ref,
+           bound={k: max(TOL, 3 * ref[k]) for k in ref})
     for k in ("rho", "phi", "C"):
         assert e[k] <= max(TOL, 3 * ref[k]), (e, ref)
 
@@ -343,6 +360,8 @@ def test_d3q27_geometric_wetting_1000_steps(wet):
     g.step(1000)
     o, ref = _perturbed_oracle_spread(wl, 1000)
     e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
+    record("D3Q27 sessile cap wetting %d, 1000 steps" % wet, normwise=e, perturbed_oracle_spread=ref,
+           bound={k: max(TOL, 3 * ref[k]) for k in ref})
     for k in ("rho", "phi", "C"):
         assert e[k] <= max(TOL, 3 * ref[k]), (e, ref)
 
@@ -351,8 +370,7 @@ def test_d3q27_geometric_wetting_1000_steps(wet):
 def test_d2q9_fp16_order_parameter_error_is_bounded(case):
     """Reduced-precision g storage through the D2Q9 step kernel (which keeps
     the raw halves of a tile's own nodes in shared memory): against the FP64
-    oracle after 200 steps the normwise error stays below 1e-3, the
-    accumulation of FP16 rounding (2^-11 relative) of the moving populations."""
+    oracle after 200 steps the normwise error stays below FP16_TOL."""
     wl = W.c0_sessile_drop()
     if case == "c0_interp":
         wl["params"] = W.base_params(wetting=W.WET_GEOM_INTERP, theta_deg=(60.0, 60.0, 120.0))
@@ -361,6 +379,8 @@ def test_d2q9_fp16_order_parameter_error_is_bounded(case):
     o = oracle_from_workload(wl)
     g.step(200)
     o.step(200)
-    e = normwise(g.fields(), o.fields(), o.derived, mask=wl["mask"])
-    print("D2Q9 FP16 g storage, 200 steps, normwise error vs FP64 oracle:", e)
-    assert e["phi"] < 1e-3 and e["rho"] < 1e-3 and e["C"] < 1e-3, e
+    fg, fo = g.fields(), o.fields()
+    e = normwise(fg, fo, o.derived, mask=wl["mask"])
+    record("D2Q9 FP16 g storage %s, 200 steps" % case, normwise=e, pointwise_rho=pointwise_rho(fg, fo, wl["mask"]),
+           bound=FP16_TOL)
+    assert e["phi"] < FP16_TOL and e["rho"] < FP16_TOL and e["C"] < FP16_TOL, e
