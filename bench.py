@@ -377,9 +377,10 @@ def e2e_run(wl, tlb, nsteps=1000, reps=2):
             "job": "tlb_init_fields (host FP64) + %d steps + tlb_get_fields (host FP64)" % nsteps}
 
 
-def batched_sweep(steps=10):
+def batched_sweep(steps=20):
     """The contact-angle sweep (512 D2Q9 lattices, 64^2-512^2, 43.8 M nodes):
-    all lattices advanced by tlb_step_batch (one launch per phase) against the
+    all lattices advanced by one resident batch (tlb_batch_*: the launch
+    configuration chosen by the autotuner, CUDA-graph replays) against the
     same lattices advanced one after another by tlb_step."""
     import torch
 
@@ -389,13 +390,18 @@ def batched_sweep(steps=10):
     items = W.c3_sweep()
     lats = [tlb.lattice_from_workload(W.c3_lattice(it)) for it in items]
     nodes = sum(l.N for l in lats)
-    handles = [l.h for l in lats]
-    tlb.tlb_step_batch(handles, 2)
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tlb.tlb_step_batch(handles, steps)
+    batch = tlb.Batch(lats)
+    cfg = batch.tune(reps=2)
+    t_tune = time.perf_counter() - t0
+    batch.step(2)
     torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    batch.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) * 1e-3
     for l in lats:
         l.step(1)
     torch.cuda.synchronize()
@@ -406,10 +412,16 @@ def batched_sweep(steps=10):
     ts = time.perf_counter() - t0
     for l in lats:
         l.sync()
+    names = {0: "lattice-major", 1: "interleaved", 2: "largest first"}
     res = {"workload": "c3 sweep: %d D2Q9 lattices, %d nodes" % (len(lats), nodes),
            "batched_mlups": round(nodes * steps / tb / 1e6, 1), "sequential_mlups": round(nodes * steps / ts / 1e6, 1),
            "speedup": round(ts / tb, 3), "steps": steps,
+           "tuned": {"variant": cfg["variant"], "tile_order": names[cfg["tile_order"]],
+                     "graph_depth": cfg["graph_depth"], "us_per_step": round(cfg["us_per_step"], 2),
+                     "tuning_s": round(t_tune, 3)},
+           "roofline_frac": round(algorithmic_bytes(9, nodes) / (tb / steps) / 1e9 / hbm_peak()[0], 4),
            "l2": "state %.1f GB, larger than L2" % (sum(l.device_bytes for l in lats) / 1e9)}
+    batch.close()
     for l in lats:
         l.close()
     return res
@@ -435,25 +447,20 @@ def tension_sweep(grid=4, L=96, R=24.0, steps=3000):
                         "theta_deg": [round(v, 2) for v in res[0]["theta"]]}}
 
 
-def served_mix(budget_gb=24.0, max_active=64, steps_per_round=100):
-    """Poisson arrivals (20/s) of 64 requests (drops, channels, lubricated
-    substrates; see workloads.c4_requests) into the continuous-batching
-    server; p50/p99 time from submission to result and aggregate MLUPS over
-    the makespan, against the same requests run one after another alone."""
-    import torch
-
+def _serve(reqs, budget_gb, max_active, steps_per_round, arrivals):
+    """Run the request list through the continuous-batching server: with
+    `arrivals` each request is submitted at its Poisson arrival time, else all
+    at once (a saturated server).  Time from submission to result per request
+    and aggregate MLUPS over the makespan."""
     from paper_1904_06881_gb300 import tlb
-    from paper_1904_06881_gb300 import workloads as W
 
-    reqs = W.c4_requests()
-    work = sum(w["nx"] * w["ny"] * w["nz"] * n for _, w, n in reqs)
     srv = tlb.Server(int(budget_gb * (1 << 30)), max_active=max_active, steps_per_round=steps_per_round)
     t_start = time.perf_counter()
     pending = list(range(len(reqs)))
     tickets, lat, failed = {}, {}, {}
     while len(lat) + len(failed) < len(reqs):
         now = time.perf_counter() - t_start
-        while pending and reqs[pending[0]][0] <= now:
+        while pending and (not arrivals or reqs[pending[0]][0] <= now):
             k = pending.pop(0)
             _, wl, n = reqs[k]
             tickets[k] = srv.submit(wl["lattice"], wl["nx"], wl["ny"], wl["nz"], wl["mask"], wl["rho"], wl["phi"], n,
@@ -467,14 +474,35 @@ def served_mix(budget_gb=24.0, max_active=64, steps_per_round=100):
                 lat[k] = r["done_s"] - r["submit_s"]
             elif r["state"] == tlb.REQ_FAILED:
                 failed[k] = tlb.ERRORS.get(r["status"], r["status"])
-        if not tickets and pending:
+        if len(lat) + len(failed) == len(tickets) and pending:
             time.sleep(max(0.0, reqs[pending[0]][0] - (time.perf_counter() - t_start)))
     makespan = time.perf_counter() - t_start
     srv.close()
-    done_work = sum(reqs[k][1]["nx"] * reqs[k][1]["ny"] * reqs[k][1]["nz"] * reqs[k][2] for k in lat)
-    # the completed requests one after another, each alone
+    work = sum(reqs[k][1]["nx"] * reqs[k][1]["ny"] * reqs[k][1]["nz"] * reqs[k][2] for k in lat)
+    lats = np.array([lat[k] for k in sorted(lat)]) if lat else np.zeros(1)
+    return {"completed": len(lat), "failed": {str(k): v for k, v in failed.items()},
+            "p50_s": round(float(np.percentile(lats, 50)), 4), "p99_s": round(float(np.percentile(lats, 99)), 4),
+            "aggregate_mlups": round(work / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
+            "node_steps": work}, sorted(lat)
+
+
+def served_mix(budget_gb=48.0, max_active=64, steps_per_round=100):
+    """The served mix (workloads.c4_requests: 256 requests of drops, channels,
+    lubricated substrates, lenses and drop trains, 64^2-1024^2 and 96^3-192^3,
+    liquid-gas and liquid-liquid) through the continuous-batching server,
+    once with Poisson arrivals (20/s) and once with every request submitted
+    at the start (saturated), against the same requests run one after
+    another alone through tlb_step (the same kernels, so the same results)."""
+    import torch
+
+    from paper_1904_06881_gb300 import tlb
+    from paper_1904_06881_gb300 import workloads as W
+
+    reqs = W.c4_requests()
+    poisson, done = _serve(reqs, budget_gb, max_active, steps_per_round, arrivals=True)
+    saturated, _ = _serve(reqs, budget_gb, max_active, steps_per_round, arrivals=False)
     t0 = time.perf_counter()
-    for k in sorted(lat):
+    for k in done:
         _, wl, n = reqs[k]
         l = tlb.lattice_from_workload(wl)
         l.step(n)
@@ -482,14 +510,11 @@ def served_mix(budget_gb=24.0, max_active=64, steps_per_round=100):
         l.close()
     torch.cuda.synchronize()
     tseq = time.perf_counter() - t0
-    lats = np.array([lat[k] for k in sorted(lat)])
-    work = done_work
-    return {"workload": "c4 served mix: %d requests, Poisson 20/s, %.2f G node-steps completed"
-                        % (len(reqs), work / 1e9),
-            "completed": len(lat), "failed": {str(k): v for k, v in failed.items()},
-            "p50_s": round(float(np.percentile(lats, 50)), 4), "p99_s": round(float(np.percentile(lats, 99)), 4),
-            "aggregate_mlups": round(work / makespan / 1e6, 1), "makespan_s": round(makespan, 3),
-            "arrival_span_s": round(reqs[-1][0], 3), "sequential_alone_mlups": round(work / tseq / 1e6, 1),
+    work = poisson["node_steps"]
+    return {"workload": "c4 served mix: %d requests (%.1f G node-steps), Poisson 20/s over %.1f s"
+                        % (len(reqs), sum(w["nx"] * w["ny"] * w["nz"] * n for _, w, n in reqs) / 1e9, reqs[-1][0]),
+            "poisson": poisson, "saturated": saturated,
+            "sequential_alone_mlups": round(work / tseq / 1e6, 1), "sequential_alone_s": round(tseq, 3),
             "server": {"budget_gb": budget_gb, "max_active": max_active, "steps_per_round": steps_per_round}}
 
 

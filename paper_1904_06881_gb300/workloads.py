@@ -240,30 +240,105 @@ def bislug_2d(H=19, L1=60, L2=60, gas=120, theta=60.0, x0=None, wetting=WET_GEOM
                 slug=dict(H=H, L1=L1, L2=L2, gas=gas, x0=x0))
 
 
-def c4_requests(seed=4, n=64, rate=20.0):
-    """Served mix: Poisson arrivals (mean `rate` per second) of requests drawn
-    from sessile drops (64^2-256^2), capillary channels (256x64-1024x64) and
-    lubricated substrates (D3Q27 48^3-96^3), with uniform random angles in
-    [30, THETA_MAX] deg (geometric interpolation) and 1000-3000 steps (2D) or
-    300-800 steps (3D).  Returns a list of (arrival_s, workload dict, steps)."""
+def lens_2d(L, R=None, ratio=None, theta=None, seed=0):
+    """2D liquid lens (Sec. III, Neumann angles): a liquid-1 (C2) disc of
+    radius R centred on the flat interface between a liquid-2 (C3) layer
+    (lower half) and gas (upper half) of a periodic L x L box."""
+    R = L / 6.0 if R is None else R
+    y, x = np.mgrid[0:L, 0:L].astype(np.float64)
+    disc = _blob(np.hypot(x - L / 2.0, y - L / 2.0), R, 2.0)
+    below = 0.5 * (1.0 - np.tanh((y - L / 2.0) / 2.0))
+    C2 = disc
+    C3 = below * (1.0 - disc)
+    rho_l, rho_g = RHO_L, (RHO_L / ratio if ratio else RHO_G)
+    rho, phi = phase_fields(C2, C3, rho_l, rho_g)
+    p = base_params(rho_l=rho_l, rho_g=rho_g)
+    return dict(name="lens_%d" % L, lattice=D2Q9, nx=L, ny=L, nz=1, params=p,
+                mask=np.zeros((1, L, L), np.uint8), rho=rho[None], phi=phi[None])
+
+
+def drop_train_2d(nx, ny=64, ndrop=4, ratio=None, theta=60.0):
+    """A train of `ndrop` liquid-1 drops (radius ny/5) alternating with
+    liquid-2 drops, resting on the bottom wall of a periodic channel (solid
+    rows y = 0 and y = ny - 1); geometric interpolation at `theta`."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    R = ny / 5.0
+    C2 = np.zeros_like(x)
+    C3 = np.zeros_like(x)
+    for k in range(ndrop):
+        xc = (k + 0.5) * nx / ndrop
+        blob = _blob(np.hypot(x - xc, y - 0.5), R, 2.0)
+        if k % 2 == 0:
+            C2 = np.maximum(C2, blob)
+        else:
+            C3 = np.maximum(C3, blob)
+    rho_l, rho_g = RHO_L, (RHO_L / ratio if ratio else RHO_G)
+    rho, phi = phase_fields(C2, C3, rho_l, rho_g)
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0, :] = 1
+    mask[ny - 1, :] = 1
+    p = base_params(wetting=WET_GEOM_INTERP, theta_deg=(theta, theta, 90.0), rho_l=rho_l, rho_g=rho_g)
+    return dict(name="drop_train_%dx%d" % (nx, ny), lattice=D2Q9, nx=nx, ny=ny, nz=1, params=p,
+                mask=mask[None], rho=rho[None], phi=phi[None])
+
+
+def _liquid_liquid(wl):
+    """The same geometry with the gas replaced by liquid 2 (C3): a
+    liquid-liquid request (density ratio 1)."""
+    rho_l = wl["params"]["rho_l"]
+    C1 = (wl["rho"] - rho_l) / (wl["params"]["rho_g"] - rho_l)
+    C2 = 0.5 * (1.0 + wl["phi"] / wl["params"]["chi"] - C1)
+    C3 = 1.0 - C2
+    rho, phi = phase_fields(C2, C3, rho_l, wl["params"]["rho_g"], wl["params"]["chi"])
+    out = dict(wl)
+    out["rho"], out["phi"] = rho, phi
+    out["name"] = wl["name"] + "_ll"
+    return out
+
+
+def c4_requests(seed=4, n=256, rate=20.0, sizes_2d=(64, 128, 256, 512, 1024), sizes_3d=(96, 128, 160, 192)):
+    """Served mix: Poisson arrivals (mean `rate` per second) of n requests:
+    sessile drops (L^2, L in sizes_2d), capillary channels (nx x 64,
+    nx in 256-1024), lubricated substrates (D3Q27 n^3, n in sizes_3d), liquid
+    lenses and drop trains (2D); uniform random angles in [30, THETA_MAX]
+    deg; the liquid-gas density ratio log-uniform between 2 and the
+    workloads' 14.1 (the gas density rho_l / ratio), or a liquid-liquid
+    request (ratio 1: the gas replaced by liquid 2) in one request of eight.
+    Steps: 2D 1000-5000, 3D 500-2000.  Returns a list of (arrival_s,
+    workload dict, steps)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    ratio_max = RHO_L / RHO_G
     out = []
     for k in range(n):
-        kind = rng.choice(["drop", "channel", "lubricated"], p=[0.5, 0.35, 0.15])
+        kind = rng.choice(["drop", "channel", "lubricated", "lens", "train"], p=[0.35, 0.2, 0.1, 0.15, 0.2])
         th = float(rng.uniform(30.0, THETA_MAX))
+        ll = rng.uniform() < 0.125
+        ratio = float(np.exp(rng.uniform(np.log(2.0), np.log(ratio_max))))
         if kind == "drop":
-            L = int(rng.choice([64, 128, 256]))
-            wl = c3_lattice(dict(L=L, theta=th, wetting=WET_GEOM_INTERP))
-            steps = int(rng.integers(1000, 3001))
+            L = int(rng.choice(sizes_2d))
+            mask, rho, phi = sessile_drop_2d(L, L, L / 4.0, xc=L / 2.0, yc=0.5, rho_g=RHO_L / ratio)
+            wl = dict(name="drop_%d" % L, lattice=D2Q9, nx=L, ny=L, nz=1, mask=mask, rho=rho, phi=phi,
+                      params=base_params(wetting=WET_GEOM_INTERP, theta_deg=(th, th, 90.0), rho_g=RHO_L / ratio))
+            steps = int(rng.integers(1000, 5001))
         elif kind == "channel":
             nx = int(rng.choice([256, 512, 1024]))
             wl = c1_capillary(nx=nx, ny=64, x_in=nx // 4, x_out=nx - nx // 16)
             wl["params"] = base_params(wetting=WET_GEOM_INTERP, theta_deg=(th, 60.0, 120.0))
-            steps = int(rng.integers(1000, 3001))
+            steps = int(rng.integers(1000, 5001))
+        elif kind == "lens":
+            wl = lens_2d(int(rng.choice(sizes_2d[:4])), ratio=ratio)
+            steps = int(rng.integers(1000, 5001))
+        elif kind == "train":
+            wl = drop_train_2d(int(rng.choice([256, 512, 1024])), 64, ndrop=int(rng.integers(2, 7)), ratio=ratio,
+                               theta=th)
+            steps = int(rng.integers(1000, 5001))
         else:
-            n3 = int(rng.choice([48, 64, 96]))
+            n3 = int(rng.choice(sizes_3d))
             wl = c2_lubricated(nx=n3, ny=n3, nz=n3, R=n3 / 6.0, lub=3, gap=2, kw_rho=0.02)
-            steps = int(rng.integers(300, 801))
+            steps = int(rng.integers(500, 2001))
+            ll = False
+        if ll:
+            wl = _liquid_liquid(wl)
         out.append((float(t[k]), wl, steps))
     return out

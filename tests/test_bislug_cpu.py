@@ -60,3 +60,66 @@ def test_package_centroid_unwraps():
     C[2, 1:-1, :5] = 1.0
     assert abs(B.centroid(C) - 99.5) < 1e-9
     assert abs(B.centroid(C, prev=-0.4) - (-0.5)) < 1e-9
+
+
+def _arc_side(x, y, x0, ymid, H, theta_left):
+    """Indicator (tanh edge of width 4) of the side left of a circular arc
+    that crosses the channel centre line at x0 and meets both walls at
+    theta_left, measured in the left phase."""
+    R = (H / 2.0) / abs(math.cos(math.radians(theta_left)))
+    if theta_left < 90.0:
+        d = np.hypot(x - (x0 + R), y - ymid) - R          # centre on the right: left side outside
+        return 0.5 * (1.0 + np.tanh(d / 2.0))
+    d = np.hypot(x - (x0 - R), y - ymid) - R              # centre on the left: left side inside
+    return 0.5 * (1.0 - np.tanh(d / 2.0))
+
+
+def test_dynamic_angles_of_synthetic_train():
+    """Three circular interfaces of known angles (rear gas | C2 at theta_21 =
+    70 deg in C2, C2 | C3 at theta_23 = 100 deg in C2, front C3 | gas at
+    theta_31 = 55 deg in C3) in a channel of height 39 are measured within
+    0.3 deg, wherever the train sits on the periodic ring."""
+    H, nx = 39, 420
+    ny = H + 2
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    ymid = (ny - 1) / 2.0
+    La = _arc_side(x, y, 150.0, ymid, H, 180.0 - 70.0)
+    Lb = _arc_side(x, y, 230.0, ymid, H, 100.0)
+    Lc = _arc_side(x, y, 310.0, ymid, H, 55.0)
+    C2, C3 = np.clip(Lb - La, 0, 1), np.clip(Lc - Lb, 0, 1)
+    rl, rg = 6.0, 0.4
+    for shift in (0, 250):
+        c2, c3 = np.roll(C2, shift, 1), np.roll(C3, shift, 1)
+        C1 = 1.0 - c2 - c3
+        rho = rl + C1 * (rg - rl)
+        f = dict(C=np.stack([C1, c2, c3])[:, None], rho=rho[None])
+        a = B.dynamic_angles(f, rl, rg)
+        assert abs(a["theta_21"] - 70.0) < 0.3, a
+        assert abs(a["theta_23"] - 100.0) < 0.3, a
+        assert abs(a["theta_31"] - 55.0) < 0.3, a
+
+
+def test_cox_function_limits_and_symmetry():
+    """Eq. Coxlful: exchanging the two fluids (theta -> pi - theta, lambda ->
+    1/lambda) scales f by 1/lambda exactly; for an inviscid receding fluid
+    (lambda -> 0... the advancing one alone, Voinov's limit) g(theta) ->
+    theta^3 / 9 at small angles; g increases with theta."""
+    for th in (0.3, 1.0, 2.0, 2.8):
+        for lam in (0.5, 2.0, 14.0):
+            assert math.isclose(lam * B.cox_f(math.pi - th, 1.0 / lam), B.cox_f(th, lam), rel_tol=1e-12)
+    assert math.isclose(B.cox_g(0.05, 0.0), 0.05 ** 3 / 9.0, rel_tol=1e-3)
+    gs = [B.cox_g(math.radians(t), 14.0) for t in (30, 60, 90, 120, 150)]
+    assert all(b > a for a, b in zip(gs, gs[1:]))
+
+
+def test_slip_length_recovers_a_planted_slope():
+    """Dynamic angles built from Eq. Coxapparent with a known L_s give it back."""
+    from scipy.optimize import brentq
+
+    lam, tw, Lc, Ls = 14.0, 60.0, 39.0, 2.5
+    m = math.log(Lc / Ls)
+    g0 = B.cox_g(math.radians(tw), lam)
+    cas = [1e-3, 2e-3, 4e-3]
+    ths = [math.degrees(brentq(lambda t: B.cox_g(t, lam) - g0 - ca * m, 1e-3, math.pi - 1e-3)) for ca in cas]
+    ls, mm = B.slip_length(ths, cas, tw, lam, Lc)
+    assert math.isclose(ls, Ls, rel_tol=1e-4) and math.isclose(mm, m, rel_tol=1e-5)
