@@ -64,7 +64,17 @@ typedef struct {
     double kw_rho, kw_phi;       /* force-method strengths (Eq. forceBC) */
     int    g_fp16;               /* 1: reduced-precision g storage: the rest population g_0 in
                                     FP32, the moving populations in FP16 scaled by 16 */
+    int    eos;                  /* TLB_EOS_*: the equation of state behind Psi_eos (Sec. II.A names
+                                    Carnahan-Starling, used throughout the paper, van der Waals and
+                                    Peng-Robinson as EOS the model hosts); default Carnahan-Starling */
+    double omega;                /* Peng-Robinson acentric factor (default 0.344) */
+    double nu[3];                /* kinematic viscosity of C1 (gas), C2, C3; all 0 (default): one
+                                    beta for the whole fluid, as in the paper.  Otherwise the local
+                                    beta = 1/(6 nu + 1) with nu the concentration-weighted mean of
+                                    the three (concentrations clipped to [0, 1]); an extension, the
+                                    paper has one viscosity (Sec. II.C) */
 } tlb_params;
+enum { TLB_EOS_CS = 0, TLB_EOS_VDW = 1, TLB_EOS_PR = 2 };
 
 /* Constants derived at creation (host FP64). */
 typedef struct {
@@ -73,6 +83,7 @@ typedef struct {
     double C, Psi0;              /* constants of Eq. PsiEOS */
     double Tc;                   /* critical temperature of the EOS */
     double kappa_rr, kappa_pp, kappa_rp;   /* gradient coefficients (Sec. II.B) */
+    double aA;                   /* attraction constant in use: a (CS, vdW) or a A(T) (PR) */
 } tlb_derived;
 
 typedef struct tlb_ctx tlb_ctx;
@@ -103,6 +114,12 @@ int tlb_params_default(tlb_params *p);
 int tlb_create(int lattice, int nx, int ny, int nz, const double densities[2], const double kappas[3],
                const double viscosities[3], int wetting, const double angles_deg[3], tlb_ctx **out);
 int tlb_create_ex(const tlb_params *p, tlb_ctx **out);
+/* Host only (no device call): the constants a context created from p would
+ * use -- temperature from the density ratio, a and b after rescaling,
+ * coexistence densities, C and Psi0 of Psi_eos (Sec. II.A), T_c, gradient
+ * coefficients (Sec. II.B).  TLB_E_INVAL for invalid parameters or no
+ * coexistence. */
+int tlb_derive(const tlb_params *p, tlb_derived *out);
 
 /* Force-wetting calibration.  Eq. forceBC (Sec. IV) sets the wall's wetting
  * through strengths kappa^w, not angles; the paper maps one to the other by

@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
                 ("R", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double),
                 ("beta", ctypes.c_double), ("tau_g", ctypes.c_double), ("Gamma", ctypes.c_double),
                 ("wetting", ctypes.c_int), ("theta_deg", ctypes.c_double * 3),
-                ("kw_rho", ctypes.c_double), ("kw_phi", ctypes.c_double)]
+                ("kw_rho", ctypes.c_double), ("kw_phi", ctypes.c_double), ("eos", ctypes.c_int),
+                ("omega", ctypes.c_double), ("nu", ctypes.c_double * 3)]
 
 
 class Derived(ctypes.Structure):
@@ -72,6 +73,14 @@ def lib():
         L.tlbo_eos_psi.argtypes = [d, d, d, d, d, d]
         L.tlbo_eos_dpsi.restype = d
         L.tlbo_eos_dpsi.argtypes = [d, d, d, d, d, d]
+        for name in ("tlbo_eos_psi_k", "tlbo_eos_dpsi_k"):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [i, d, d, d, d, d, d, d]
+        L.tlbo_eos_p_k.restype = d
+        L.tlbo_eos_p_k.argtypes = [i, d, d, d, d, d, d]
+        L.tlbo_eos_critical_T_k.restype = d
+        L.tlbo_eos_critical_T_k.argtypes = [i, d, d, d, d]
+        L.tlbo_eos_coexistence_k.argtypes = [i, d, d, d, d, d, dp]
         L.tlbo_lattice.argtypes = [i, ctypes.POINTER(ctypes.c_int), dp]
         L.tlbo_feq.argtypes = [i, d, dp, dp]
         L.tlbo_entropy.restype = d
@@ -121,6 +130,27 @@ def eos_coexistence(a, b, R, T):
     if rc != 0:
         raise ValueError("no coexistence at T=%g" % T)
     return dict(rho_g=out[0], rho_l=out[1], C=out[2], Psi0=out[3])
+
+
+EOS_CS, EOS_VDW, EOS_PR = 0, 1, 2
+
+
+def eos_k(kind, omega=0.344):
+    """Functions of the equation of state `kind` (EOS_*): psi, dpsi, p,
+    critical_T, coexistence (same arguments as the Carnahan-Starling ones)."""
+    L = lib()
+
+    def coexistence(a, b, R, T):
+        out = np.zeros(4)
+        if L.tlbo_eos_coexistence_k(kind, omega, a, b, R, T, _dptr(out)) != 0:
+            raise ValueError("no coexistence at T=%g" % T)
+        return dict(rho_g=out[0], rho_l=out[1], C=out[2], Psi0=out[3])
+
+    return dict(psi=lambda r, a, b, R, T, C: L.tlbo_eos_psi_k(kind, omega, r, a, b, R, T, C),
+                dpsi=lambda r, a, b, R, T, C: L.tlbo_eos_dpsi_k(kind, omega, r, a, b, R, T, C),
+                p=lambda r, a, b, R, T: L.tlbo_eos_p_k(kind, omega, r, a, b, R, T),
+                critical_T=lambda a, b, R=1.0: L.tlbo_eos_critical_T_k(kind, omega, a, b, R),
+                coexistence=coexistence)
 
 
 def eos_psi(rho, a, b, R, T, C):
@@ -176,7 +206,8 @@ class Oracle:
     def __init__(self, lattice=D2Q9, nx=64, ny=64, nz=1, lam=(0.6, 1.0, 1.0),
                  kappa=(0.01, 1.0, 1.0), chi=5.0, a=0.037, b=0.2, R=1.0, rho_l=1.0,
                  rho_g=1e-3, beta=0.5, tau_g=1.0, Gamma=1.0, wetting=WET_FORCE,
-                 theta_deg=(90.0, 90.0, 90.0), kw_rho=0.0, kw_phi=0.0):
+                 theta_deg=(90.0, 90.0, 90.0), kw_rho=0.0, kw_phi=0.0, eos=0, omega=0.344,
+                 nu=(0.0, 0.0, 0.0)):
         p = Params()
         p.lattice, p.nx, p.ny, p.nz = lattice, nx, ny, nz
         p.lam[:] = list(lam)
@@ -187,6 +218,8 @@ class Oracle:
         p.wetting = wetting
         p.theta_deg[:] = list(theta_deg)
         p.kw_rho, p.kw_phi = kw_rho, kw_phi
+        p.eos, p.omega = eos, omega
+        p.nu[:] = list(nu)
         self.params = p
         self.lattice = lattice
         self.shape = (nz, ny, nx)
@@ -269,7 +302,8 @@ def from_workload(wl, **over):
     o = Oracle(lattice=wl["lattice"], nx=wl["nx"], ny=wl["ny"], nz=wl["nz"], lam=p["lam"], kappa=p["kappa"],
                chi=p["chi"], a=p["a"], b=p["b"], R=p["R"], rho_l=p["rho_l"], rho_g=p["rho_g"], beta=p["beta"],
                tau_g=p["tau_g"], Gamma=p["Gamma"], wetting=p["wetting"], theta_deg=p["theta_deg"],
-               kw_rho=p["kw_rho"], kw_phi=p["kw_phi"])
+               kw_rho=p["kw_rho"], kw_phi=p["kw_phi"], eos=p.get("eos", 0), omega=p.get("omega", 0.344),
+               nu=p.get("nu", (0.0, 0.0, 0.0)))
     o.set_solid(wl["mask"])
     o.init_fields(wl["rho"], wl["phi"])
     return o

@@ -117,44 +117,89 @@ static void setup_lattice(tlbo_ctx *ctx)
 }
 
 /* ------------------------------------------------------------------ */
-/* Carnahan-Starling EOS (Eq. PsiEOS and its printed derivative).       */
+/* Equations of state.  Carnahan-Starling: Eq. PsiEOS and its printed   */
+/* derivative.  The paper names van der Waals and Peng-Robinson as      */
+/* other EOS the model hosts (Sec. II.A); their Psi are the integrals   */
+/* Psi/rho = int p/rho^2 drho of the textbook pressures (constant C):    */
+/*   vdW: p = rho R T/(1 - b rho) - a rho^2,                              */
+/*        Psi = rho (C - a rho + R T ln(rho/(1 - b rho)));                */
+/*   PR:  p = rho R T/(1 - b rho) - a A rho^2/(1 + 2 b rho - b^2 rho^2),   */
+/*        Psi = rho (C + R T ln(rho/(1 - b rho))                          */
+/*              - a A/(2 sqrt2 b) ln((b rho + sqrt2 - 1)/(sqrt2 + 1 - b rho))),*/
+/*        A = (1 + k (1 - sqrt(T/T_c)))^2, k = 0.37464 + 1.54226 omega     */
+/*        - 0.26992 omega^2, T_c = (0.07780/0.45724) a/(b R).             */
 /* ------------------------------------------------------------------ */
-double tlbo_eos_psi(double rho, double a, double b, double R, double T, double C)
+static double pr_alpha(double omega, double a, double b, double R, double T)
 {
+    double k = 0.37464 + 1.54226 * omega - 0.26992 * omega * omega;
+    double Tc = (0.07780 / 0.45724) * a / (b * R);
+    double s = 1.0 + k * (1.0 - sqrt(T / Tc));
+    return s * s;
+}
+
+double tlbo_eos_psi_k(int kind, double omega, double rho, double a, double b, double R, double T, double C)
+{
+    if (kind == TLBO_EOS_VDW) return rho * (C - a * rho + R * T * log(rho / (1.0 - b * rho)));
+    if (kind == TLBO_EOS_PR) {
+        double aa = a * pr_alpha(omega, a, b, R, T), r2 = sqrt(2.0);
+        return rho * (C + R * T * log(rho / (1.0 - b * rho)) -
+                      aa / (2.0 * r2 * b) * log((b * rho + r2 - 1.0) / (r2 + 1.0 - b * rho)));
+    }
     double br = b * rho;
     return rho * (C - a * rho - 8.0 * R * T * (br - 6.0) / ((br - 4.0) * (br - 4.0)) +
                   R * T * log(rho));
 }
 
-double tlbo_eos_dpsi(double rho, double a, double b, double R, double T, double C)
+double tlbo_eos_dpsi_k(int kind, double omega, double rho, double a, double b, double R, double T, double C)
 {
+    if (kind == TLBO_EOS_VDW)
+        return C - 2.0 * a * rho + R * T * log(rho / (1.0 - b * rho)) + R * T / (1.0 - b * rho);
+    if (kind == TLBO_EOS_PR) {
+        double aa = a * pr_alpha(omega, a, b, R, T), r2 = sqrt(2.0), br = b * rho;
+        return C + R * T * log(rho / (1.0 - br)) + R * T / (1.0 - br) -
+               aa / (2.0 * r2 * b) * log((br + r2 - 1.0) / (r2 + 1.0 - br)) -
+               aa * rho / (1.0 + 2.0 * br - br * br);
+    }
     double br = b * rho;
     double q = br - 4.0;
     return C - 2.0 * a * rho + R * T * (1.0 + log(rho)) + 16.0 * R * T * (br - 12.0) / (q * q * q);
 }
 
-/* p_eos = rho dPsi/drho - Psi (Sec. II.A); independent of C. */
-static double eos_p(double rho, double a, double b, double R, double T)
+double tlbo_eos_psi(double rho, double a, double b, double R, double T, double C)
 {
-    return rho * tlbo_eos_dpsi(rho, a, b, R, T, 0.0) - tlbo_eos_psi(rho, a, b, R, T, 0.0);
+    return tlbo_eos_psi_k(TLBO_EOS_CS, 0.0, rho, a, b, R, T, C);
 }
 
-static double eos_dp(double rho, double a, double b, double R, double T)
+double tlbo_eos_dpsi(double rho, double a, double b, double R, double T, double C)
+{
+    return tlbo_eos_dpsi_k(TLBO_EOS_CS, 0.0, rho, a, b, R, T, C);
+}
+
+/* p_eos = rho dPsi/drho - Psi (Sec. II.A); independent of C. */
+double tlbo_eos_p_k(int kind, double omega, double rho, double a, double b, double R, double T)
+{
+    return rho * tlbo_eos_dpsi_k(kind, omega, rho, a, b, R, T, 0.0) - tlbo_eos_psi_k(kind, omega, rho, a, b, R, T, 0.0);
+}
+
+static double eos_dp(int kind, double om, double rho, double a, double b, double R, double T)
 {
     double h = 1e-6 * rho;
-    return (eos_p(rho + h, a, b, R, T) - eos_p(rho - h, a, b, R, T)) / (2.0 * h);
+    return (tlbo_eos_p_k(kind, om, rho + h, a, b, R, T) - tlbo_eos_p_k(kind, om, rho - h, a, b, R, T)) / (2.0 * h);
 }
+
+/* largest density of the EOS (packing limit) */
+static double eos_rmax(int kind, double b) { return kind == TLBO_EOS_CS ? 4.0 / b : 1.0 / b; }
 
 /* Spinodal densities: the interval where dp/drho < 0, scanned on a fine grid
  * and refined by bisection.  Returns 0 if the EOS has no unstable branch. */
-static int eos_spinodal(double a, double b, double R, double T, double *s1, double *s2)
+static int eos_spinodal(int kind, double om, double a, double b, double R, double T, double *s1, double *s2)
 {
     const int M = 4000;
-    double rmax = 4.0 / b;
+    double rmax = eos_rmax(kind, b);
     int first = -1, last = -1;
     for (int k = 1; k < M; ++k) {
         double r = rmax * k / M;
-        if (eos_dp(r, a, b, R, T) < 0.0) {
+        if (eos_dp(kind, om, r, a, b, R, T) < 0.0) {
             if (first < 0) first = k;
             last = k;
         }
@@ -163,37 +208,39 @@ static int eos_spinodal(double a, double b, double R, double T, double *s1, doub
     double lo = rmax * (first - 1) / M, hi = rmax * first / M;
     for (int it = 0; it < 200; ++it) {
         double m = 0.5 * (lo + hi);
-        if (eos_dp(m, a, b, R, T) < 0.0) hi = m; else lo = m;
+        if (eos_dp(kind, om, m, a, b, R, T) < 0.0) hi = m; else lo = m;
     }
     *s1 = hi;
     lo = rmax * last / M; hi = rmax * (last + 1) / M;
     for (int it = 0; it < 200; ++it) {
         double m = 0.5 * (lo + hi);
-        if (eos_dp(m, a, b, R, T) < 0.0) lo = m; else hi = m;
+        if (eos_dp(kind, om, m, a, b, R, T) < 0.0) lo = m; else hi = m;
     }
     *s2 = lo;
     return 1;
 }
 
-double tlbo_eos_critical_T(double a, double b, double R)
+double tlbo_eos_critical_T_k(int kind, double omega, double a, double b, double R)
 {
     /* T_c is the largest T with an unstable branch; bracket on a/(bR). */
     double lo = 0.05 * a / (b * R), hi = 1.0 * a / (b * R);
     double s1, s2;
     for (int it = 0; it < 100; ++it) {
         double m = 0.5 * (lo + hi);
-        if (eos_spinodal(a, b, R, m, &s1, &s2)) lo = m; else hi = m;
+        if (eos_spinodal(kind, omega, a, b, R, m, &s1, &s2)) lo = m; else hi = m;
     }
     return 0.5 * (lo + hi);
 }
 
+double tlbo_eos_critical_T(double a, double b, double R) { return tlbo_eos_critical_T_k(TLBO_EOS_CS, 0.0, a, b, R); }
+
 /* Root of p(rho) = P on [lo, hi] by bisection (p monotone there). */
-static double eos_root(double a, double b, double R, double T, double P, double lo, double hi)
+static double eos_root(int kind, double om, double a, double b, double R, double T, double P, double lo, double hi)
 {
-    double plo = eos_p(lo, a, b, R, T) - P;
+    double plo = tlbo_eos_p_k(kind, om, lo, a, b, R, T) - P;
     for (int it = 0; it < 300; ++it) {
         double m = 0.5 * (lo + hi);
-        double pm = eos_p(m, a, b, R, T) - P;
+        double pm = tlbo_eos_p_k(kind, om, m, a, b, R, T) - P;
         if ((pm < 0.0) == (plo < 0.0)) { lo = m; plo = pm; } else hi = m;
         if (hi - lo <= 1e-17 * hi) break;
     }
@@ -203,34 +250,39 @@ static double eos_root(double a, double b, double R, double T, double P, double 
 /* Coexistence: equal pressure and equal chemical potential dPsi/drho of the
  * gas and liquid branches (common tangent, Sec. II.A).  Bisection on the
  * common pressure P between the spinodal pressures. */
-int tlbo_eos_coexistence(double a, double b, double R, double T, double out[4])
+int tlbo_eos_coexistence_k(int kind, double om, double a, double b, double R, double T, double out[4])
 {
     double s1, s2;
-    if (!eos_spinodal(a, b, R, T, &s1, &s2)) return -1;
-    double Plo = eos_p(s2, a, b, R, T), Phi = eos_p(s1, a, b, R, T);
+    if (!eos_spinodal(kind, om, a, b, R, T, &s1, &s2)) return -1;
+    double Plo = tlbo_eos_p_k(kind, om, s2, a, b, R, T), Phi = tlbo_eos_p_k(kind, om, s1, a, b, R, T);
     if (Plo < 0.0) Plo = 0.0;
-    double rg = 0, rl = 0;
+    double rg = 0, rl = 0, rtop = eos_rmax(kind, b) * (1.0 - 1e-15);
     for (int it = 0; it < 200; ++it) {
         double P = 0.5 * (Plo + Phi);
-        rg = eos_root(a, b, R, T, P, 1e-300, s1);
-        rl = eos_root(a, b, R, T, P, s2, 4.0 / b * (1.0 - 1e-15));
-        double dmu = tlbo_eos_dpsi(rl, a, b, R, T, 0.0) - tlbo_eos_dpsi(rg, a, b, R, T, 0.0);
+        rg = eos_root(kind, om, a, b, R, T, P, 1e-300, s1);
+        rl = eos_root(kind, om, a, b, R, T, P, s2, rtop);
+        double dmu = tlbo_eos_dpsi_k(kind, om, rl, a, b, R, T, 0.0) - tlbo_eos_dpsi_k(kind, om, rg, a, b, R, T, 0.0);
         /* d mu = dp / rho along each branch (Gibbs-Duhem), so mu(rl) - mu(rg)
          * decreases as the common pressure P rises */
         if (dmu > 0.0) Plo = P; else Phi = P;
         if (Phi - Plo <= 1e-16 * Phi) break;
     }
     double P = 0.5 * (Plo + Phi);
-    rg = eos_root(a, b, R, T, P, 1e-300, s1);
-    rl = eos_root(a, b, R, T, P, s2, 4.0 / b * (1.0 - 1e-15));
+    rg = eos_root(kind, om, a, b, R, T, P, 1e-300, s1);
+    rl = eos_root(kind, om, a, b, R, T, P, s2, rtop);
     /* C makes the common tangent horizontal: dPsi/drho = 0 at both phases,
      * so Psi(rho_g) = Psi(rho_l) = Psi0. */
-    double C = -0.5 * (tlbo_eos_dpsi(rl, a, b, R, T, 0.0) + tlbo_eos_dpsi(rg, a, b, R, T, 0.0));
+    double C = -0.5 * (tlbo_eos_dpsi_k(kind, om, rl, a, b, R, T, 0.0) + tlbo_eos_dpsi_k(kind, om, rg, a, b, R, T, 0.0));
     out[0] = rg;
     out[1] = rl;
     out[2] = C;
-    out[3] = tlbo_eos_psi(rl, a, b, R, T, C);
+    out[3] = tlbo_eos_psi_k(kind, om, rl, a, b, R, T, C);
     return 0;
+}
+
+int tlbo_eos_coexistence(double a, double b, double R, double T, double out[4])
+{
+    return tlbo_eos_coexistence_k(TLBO_EOS_CS, 0.0, a, b, R, T, out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -420,6 +472,9 @@ int tlbo_create(const tlbo_params *p, tlbo_ctx **out)
     if (p->lattice == TLBO_D2Q9 && p->nz != 1) return -1;
     if (p->lattice == TLBO_D3Q27 && p->nz < 3) return -1;
     if (!(p->rho_l > p->rho_g && p->rho_g > 0.0)) return -1;
+    if (p->eos < TLBO_EOS_CS || p->eos > TLBO_EOS_PR) return -1;
+    for (int k = 0; k < 3; ++k)
+        if (p->nu[k] < 0.0) return -1;
     tlbo_ctx *ctx = (tlbo_ctx *)calloc(1, sizeof(tlbo_ctx));
     ctx->p = *p;
     setup_lattice(ctx);
@@ -428,23 +483,25 @@ int tlbo_create(const tlbo_params *p, tlbo_ctx **out)
     /* Density ratio r = rho_l/rho_g fixes T (bisection on T/T_c), then a and b
      * are scaled by s = rho_l(T)/rho_l_target, which keeps T_c and the ratio
      * and moves the coexistence densities to the targets. */
-    double Tc = tlbo_eos_critical_T(p->a, p->b, p->R);
+    const int K = p->eos;
+    const double om = p->omega;
+    double Tc = tlbo_eos_critical_T_k(K, om, p->a, p->b, p->R);
     double ratio = p->rho_l / p->rho_g, co[4];
     double lo = 0.05, hi = 0.9999;
     for (int it = 0; it < 60; ++it) {
         double m = 0.5 * (lo + hi);
-        if (tlbo_eos_coexistence(p->a, p->b, p->R, m * Tc, co) != 0) { hi = m; continue; }
+        if (tlbo_eos_coexistence_k(K, om, p->a, p->b, p->R, m * Tc, co) != 0) { hi = m; continue; }
         if (co[1] / co[0] > ratio) lo = m; else hi = m;
     }
     double T = 0.5 * (lo + hi) * Tc;
-    tlbo_eos_coexistence(p->a, p->b, p->R, T, co);
+    tlbo_eos_coexistence_k(K, om, p->a, p->b, p->R, T, co);
     double s = co[1] / p->rho_l;
     ctx->d.T = T;
     ctx->d.R = p->R;
     ctx->d.a = p->a * s;
     ctx->d.b = p->b * s;
     ctx->d.Tc = Tc;
-    tlbo_eos_coexistence(ctx->d.a, ctx->d.b, p->R, T, co);
+    tlbo_eos_coexistence_k(K, om, ctx->d.a, ctx->d.b, p->R, T, co);
     ctx->d.rho_g = co[0];
     ctx->d.rho_l = co[1];
     ctx->d.C = co[2];
@@ -717,8 +774,8 @@ static void thermo(tlbo_ctx *ctx)
         /* Bulk free energy and chemical potentials (Eq. BulkEnergy and its
          * derivatives with dC2/drho = dC3/drho = 1/(2 drho), dC2/dphi =
          * -dC3/dphi = 1/(2 chi)). */
-        double psi = tlbo_eos_psi(r0, d->a, d->b, d->R, d->T, d->C);
-        double dpsi = tlbo_eos_dpsi(r0, d->a, d->b, d->R, d->T, d->C);
+        double psi = tlbo_eos_psi_k(p->eos, p->omega, r0, d->a, d->b, d->R, d->T, d->C);
+        double dpsi = tlbo_eos_dpsi_k(p->eos, p->omega, r0, d->a, d->b, d->R, d->T, d->C);
         double fb = 0.5 * p->lambda[0] * (psi - d->Psi0) +
                     0.5 * p->lambda[1] * C2 * C2 * (1 - C2) * (1 - C2) +
                     0.5 * p->lambda[2] * C3 * C3 * (1 - C3) * (1 - C3);
@@ -867,10 +924,27 @@ static int collide(tlbo_ctx *ctx)
         } else {
             bad = 1;
         }
+        double beta = p->beta;
+        if (p->nu[0] > 0.0 || p->nu[1] > 0.0 || p->nu[2] > 0.0) {
+            /* viscosity of the local mixture: the concentration-weighted mean
+             * of the components' kinematic viscosities (concentrations
+             * clipped to [0, 1]), nu = (1/beta - 1)/6 */
+            const tlbo_derived *d = &ctx->d;
+            double C1 = (r - d->rho_l) / (d->rho_g - d->rho_l);
+            double C2 = 0.5 * (1.0 + ctx->phi[n] / p->chi - C1), C3 = 0.5 * (1.0 - ctx->phi[n] / p->chi - C1);
+            double c[3] = {C1, C2, C3}, ws = 0.0, nu = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                double ck = c[k] < 0.0 ? 0.0 : (c[k] > 1.0 ? 1.0 : c[k]);
+                ws += ck;
+                nu += ck * p->nu[k];
+            }
+            nu /= ws;
+            beta = 1.0 / (6.0 * nu + 1.0);
+        }
         for (int i = 0; i < Q; ++i) {
             double fi = ctx->f[i * N + n];
             /* Eq. ELBMequation */
-            ctx->fs[i * N + n] = fi + al * p->beta * (feq[i] - fi) + (feqd[i] - feq[i]);
+            ctx->fs[i * N + n] = fi + al * beta * (feq[i] - fi) + (feqd[i] - feq[i]);
         }
         double geq[MAXQ];
         geq_t(&ctx->L, ctx->phi[n], v, ctx->mup[n], p->Gamma, geq);

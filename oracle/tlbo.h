@@ -48,7 +48,11 @@ typedef struct {
     int    wetting;                /* TLBO_WET_* */
     double theta_deg[3];           /* theta_21, theta_31, theta_23 */
     double kw_rho, kw_phi;         /* force-method strengths (Eq. forceBC) */
+    int    eos;                    /* TLBO_EOS_*: Carnahan-Starling (Eq. PsiEOS), van der Waals, Peng-Robinson */
+    double omega;                  /* Peng-Robinson acentric factor */
+    double nu[3];                  /* kinematic viscosity of C1, C2, C3; all 0: one beta for the fluid */
 } tlbo_params;
+enum { TLBO_EOS_CS = 0, TLBO_EOS_VDW = 1, TLBO_EOS_PR = 2 };
 
 /* Derived constants of a context (filled by tlbo_create). */
 typedef struct {
@@ -64,6 +68,15 @@ typedef struct tlbo_ctx tlbo_ctx;
 /* ---- thermodynamics (Sec. II.A) ---- */
 /* Critical temperature of the Carnahan-Starling EOS, found numerically. */
 double tlbo_eos_critical_T(double a, double b, double R);
+/* The same for the equation of state `kind` (TLBO_EOS_*; omega: the
+ * Peng-Robinson acentric factor): free energy Psi, dPsi/drho, pressure
+ * p = rho dPsi/drho - Psi, critical temperature, coexistence {rho_g, rho_l,
+ * C, Psi0}. */
+double tlbo_eos_psi_k(int kind, double omega, double rho, double a, double b, double R, double T, double C);
+double tlbo_eos_dpsi_k(int kind, double omega, double rho, double a, double b, double R, double T, double C);
+double tlbo_eos_p_k(int kind, double omega, double rho, double a, double b, double R, double T);
+double tlbo_eos_critical_T_k(int kind, double omega, double a, double b, double R);
+int tlbo_eos_coexistence_k(int kind, double omega, double a, double b, double R, double T, double out[4]);
 /* Gas/liquid coexistence densities at temperature T (equal pressure and
  * chemical potential); out = {rho_g, rho_l, C, Psi0}.  Returns 0 or -1. */
 int tlbo_eos_coexistence(double a, double b, double R, double T, double out[4]);

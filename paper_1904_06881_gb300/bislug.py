@@ -122,8 +122,12 @@ def dynamic_angles(fields, rho_l, rho_g, skip=3):
     C = fields["C"][:, 0]
     rho = fields["rho"][0]
     ny, nx = rho.shape
-    liq = (C[1, 1:-1] + C[2, 1:-1]).sum(axis=0)
-    shift = nx // 2 - int(np.argmax(np.convolve(np.r_[liq, liq], np.ones(nx // 4), "same")[:nx]))
+    # roll the gas column's circular centre of mass to x = 0: the train then
+    # lies inside [0, nx) without wrapping
+    gas = C[0, 1:-1].sum(axis=0)
+    ang = 2.0 * np.pi * np.arange(nx) / nx
+    xg = math.atan2(float((gas * np.sin(ang)).sum()), float((gas * np.cos(ang)).sum())) / (2.0 * np.pi) * nx
+    shift = -int(round(xg))
     rho = np.roll(rho, shift, axis=1)
     C = np.roll(C, shift, axis=2)
     mid = 0.5 * (rho_l + rho_g)

@@ -143,20 +143,45 @@ static void dev_free_all(std::vector<Block> &owned)
 // Psi_eos and its derivative.
 // ---------------------------------------------------------------------------
 namespace {
+// Equations of state on the host (FP64): Carnahan-Starling (Eq. PsiEOS,
+// the paper's), van der Waals and Peng-Robinson (named in Sec. II.A as EOS
+// the model hosts).  p and mu are the textbook pressure and chemical
+// potential; psi_printed/dpsi_printed are Psi_eos and its derivative with
+// the constant C (for CS the printed formulas).  PR: attraction a A(T),
+// A = (1 + k (1 - sqrt(T/T_c)))^2, k = 0.37464 + 1.54226 omega - 0.26992
+// omega^2, T_c = (0.07780 / 0.45724) a / (b R).
 struct CS {
     double a, b, R, T;
+    int kind = TLB_EOS_CS;
+    double omega = 0.344;
+    double aA() const
+    {
+        double k = 0.37464 + 1.54226 * omega - 0.26992 * omega * omega;
+        double s = 1.0 + k * (1.0 - std::sqrt(T / ((0.07780 / 0.45724) * a / (b * R))));
+        return a * s * s;
+    }
+    double top() const { return kind == TLB_EOS_CS ? 4.0 / b : 1.0 / b; }
     double p(double r) const
     {
+        if (kind == TLB_EOS_VDW) return r * R * T / (1 - b * r) - a * r * r;
+        if (kind == TLB_EOS_PR) return r * R * T / (1 - b * r) - aA() * r * r / (1 + 2 * b * r - b * b * r * r);
         double e = b * r / 4.0;
         return r * R * T * (1 + e + e * e - e * e * e) / std::pow(1 - e, 3) - a * r * r;
     }
     double mu(double r) const
     {
+        if (kind != TLB_EOS_CS) return dpsi_printed(r, 0.0);
         double e = b * r / 4.0;
         return R * T * (std::log(r) + (8 * e - 9 * e * e + 3 * e * e * e) / std::pow(1 - e, 3)) - 2 * a * r;
     }
     double dp(double r) const
     {
+        if (kind == TLB_EOS_VDW) return R * T / ((1 - b * r) * (1 - b * r)) - 2 * a * r;
+        if (kind == TLB_EOS_PR) {
+            double den = 1 + 2 * b * r - b * b * r * r;
+            return R * T / ((1 - b * r) * (1 - b * r)) -
+                   aA() * (2 * r * den - r * r * (2 * b - 2 * b * b * r)) / (den * den);
+        }
         double e = b * r / 4.0, om = 1 - e;
         double Z = (1 + e + e * e - e * e * e) / (om * om * om);
         double dZ = ((1 + 2 * e - 3 * e * e) * om + 3 * (1 + e + e * e - e * e * e)) / (om * om * om * om);
@@ -164,11 +189,23 @@ struct CS {
     }
     double psi_printed(double r, double C) const
     {
+        if (kind == TLB_EOS_VDW) return r * (C - a * r + R * T * std::log(r / (1 - b * r)));
+        if (kind == TLB_EOS_PR) {
+            const double s2 = std::sqrt(2.0);
+            return r * (C + R * T * std::log(r / (1 - b * r)) -
+                        aA() / (2 * s2 * b) * std::log((b * r + s2 - 1) / (s2 + 1 - b * r)));
+        }
         double br = b * r;
         return r * (C - a * r - 8 * R * T * (br - 6) / ((br - 4) * (br - 4)) + R * T * std::log(r));
     }
     double dpsi_printed(double r, double C) const
     {
+        if (kind == TLB_EOS_VDW) return C - 2 * a * r + R * T * std::log(r / (1 - b * r)) + R * T / (1 - b * r);
+        if (kind == TLB_EOS_PR) {
+            const double s2 = std::sqrt(2.0), br = b * r, A = aA();
+            return C + R * T * std::log(r / (1 - br)) + R * T / (1 - br) -
+                   A / (2 * s2 * b) * std::log((br + s2 - 1) / (s2 + 1 - br)) - A * r / (1 + 2 * br - br * br);
+        }
         double br = b * r, q = br - 4;
         return C - 2 * a * r + R * T * (1 + std::log(r)) + 16 * R * T * (br - 12) / (q * q * q);
     }
@@ -176,22 +213,22 @@ struct CS {
     bool spinodal(double &s1, double &s2) const
     {
         const int M = 6000;
-        double top = 4.0 / b;
+        double tp = top();
         int k1 = -1, k2 = -1;
         for (int k = 1; k < M; ++k)
-            if (dp(top * k / M) < 0) {
+            if (dp(tp * k / M) < 0) {
                 if (k1 < 0) k1 = k;
                 k2 = k;
             }
         if (k1 < 0) return false;
-        double lo = top * (k1 - 1) / M, hi = top * k1 / M;
+        double lo = tp * (k1 - 1) / M, hi = tp * k1 / M;
         for (int it = 0; it < 120; ++it) {
             double m = 0.5 * (lo + hi);
             (dp(m) < 0 ? hi : lo) = m;
         }
         s1 = hi;
-        lo = top * k2 / M;
-        hi = top * (k2 + 1) / M;
+        lo = tp * k2 / M;
+        hi = tp * (k2 + 1) / M;
         for (int it = 0; it < 120; ++it) {
             double m = 0.5 * (lo + hi);
             (dp(m) < 0 ? lo : hi) = m;
@@ -207,7 +244,7 @@ struct CS {
         if (!spinodal(s1, s2)) return false;
         double pmin = p(s2), pmax = p(s1);
         auto liquid_for = [&](double pg) {
-            double lo = s2, hi = 4.0 / b * (1 - 1e-14);
+            double lo = s2, hi = top() * (1 - 1e-14);
             for (int it = 0; it < 200; ++it) {
                 double m = 0.5 * (lo + hi);
                 (p(m) < pg ? lo : hi) = m;
@@ -225,6 +262,7 @@ struct CS {
             }
             lgl = hi;
         }
+        (void)pmax;
         auto G = [&](double lg) {
             double r = std::exp(lg);
             return mu(liquid_for(p(r))) - mu(r);
@@ -242,13 +280,13 @@ struct CS {
     }
 };
 
-double critical_T(double a, double b, double R)
+double critical_T(double a, double b, double R, int kind, double omega)
 {
     double lo = 0.01 * a / (b * R), hi = a / (b * R);
     for (int it = 0; it < 80; ++it) {
         double m = 0.5 * (lo + hi);
         double s1, s2;
-        CS e{a, b, R, m};
+        CS e{a, b, R, m, kind, omega};
         (e.spinodal(s1, s2) ? lo : hi) = m;
     }
     return 0.5 * (lo + hi);
@@ -273,6 +311,8 @@ extern "C" int tlb_params_default(tlb_params *p)
     p->Gamma = 1.0;
     p->wetting = TLB_WET_FORCE;
     p->theta_deg[0] = p->theta_deg[1] = p->theta_deg[2] = 90.0;
+    p->eos = TLB_EOS_CS;
+    p->omega = 0.344;
     return TLB_OK;
 }
 
@@ -283,12 +323,12 @@ static int derive_uncached(const tlb_params &p, tlb_derived &d);
 static int derive(const tlb_params &p, tlb_derived &d)
 {
     struct Key {
-        double a, b, R, rho_l, rho_g, k0, k1, k2, chi;
+        double a, b, R, rho_l, rho_g, k0, k1, k2, chi, omega, eos;
         bool operator==(const Key &o) const { return std::memcmp(this, &o, sizeof(Key)) == 0; }
     };
     static std::mutex mu;
     static std::vector<std::pair<Key, tlb_derived>> cache;
-    Key k = {p.a, p.b, p.R, p.rho_l, p.rho_g, p.kappa[0], p.kappa[1], p.kappa[2], p.chi};
+    Key k = {p.a, p.b, p.R, p.rho_l, p.rho_g, p.kappa[0], p.kappa[1], p.kappa[2], p.chi, p.omega, (double)p.eos};
     {
         std::lock_guard<std::mutex> lk(mu);
         for (auto &e : cache)
@@ -310,22 +350,22 @@ static int derive_uncached(const tlb_params &p, tlb_derived &d)
 {
     if (!(p.rho_l > p.rho_g && p.rho_g > 0)) return fail(TLB_E_INVAL, "need rho_l > rho_g > 0");
     if (!(p.a > 0 && p.b > 0 && p.R > 0)) return fail(TLB_E_INVAL, "EOS constants must be positive");
-    double Tc = critical_T(p.a, p.b, p.R);
+    double Tc = critical_T(p.a, p.b, p.R, p.eos, p.omega);
     double ratio = p.rho_l / p.rho_g;
     // the density ratio fixes T; bisection on T/T_c
     double lo = 0.02, hi = 0.9999, rg = 0, rl = 0;
     for (int it = 0; it < 64; ++it) {
         double m = 0.5 * (lo + hi);
-        CS e{p.a, p.b, p.R, m * Tc};
+        CS e{p.a, p.b, p.R, m * Tc, p.eos, p.omega};
         if (!e.coexist(rg, rl)) { hi = m; continue; }
         (rl / rg > ratio ? lo : hi) = m;
     }
     double T = 0.5 * (lo + hi) * Tc;
-    CS e0{p.a, p.b, p.R, T};
+    CS e0{p.a, p.b, p.R, T, p.eos, p.omega};
     if (!e0.coexist(rg, rl)) return fail(TLB_E_INVAL, "no coexistence for density ratio %g", ratio);
     // scaling a, b by s keeps T_c and the ratio and divides the densities by s
     double s = rl / p.rho_l;
-    CS e{p.a * s, p.b * s, p.R, T};
+    CS e{p.a * s, p.b * s, p.R, T, p.eos, p.omega};
     if (!e.coexist(rg, rl)) return fail(TLB_E_INVAL, "no coexistence after rescaling");
     d.T = T;
     d.a = e.a;
@@ -336,6 +376,7 @@ static int derive_uncached(const tlb_params &p, tlb_derived &d)
     d.rho_l = rl;
     d.C = -e.dpsi_printed(rl, 0.0);
     d.Psi0 = e.psi_printed(rl, d.C);
+    d.aA = p.eos == TLB_EOS_PR ? e.aA() : e.a;
     double drho = rl - rg;
     d.kappa_rr = p.kappa[0] + (p.kappa[1] + p.kappa[2]) / (4 * drho * drho);
     d.kappa_pp = (p.kappa[1] + p.kappa[2]) / (4 * p.chi * p.chi);
@@ -378,6 +419,10 @@ static DevParams make_dev(const tlb_params &p, const tlb_derived &d)
     q.g_fp16 = p.g_fp16;
     q.g_scale = p.g_fp16 ? 16.0f : 1.0f;        // moving g populations are O(0.1) or smaller
     q.g_unscale = p.g_fp16 ? 1.0f / 16.0f : 1.0f;
+    q.eos = p.eos;
+    q.aA = (float)d.aA;
+    q.nu_on = (p.nu[0] > 0 || p.nu[1] > 0 || p.nu[2] > 0) ? 1 : 0;
+    for (int k = 0; k < 3; ++k) q.nu[k] = (float)p.nu[k];
     return q;
 }
 
@@ -458,6 +503,9 @@ static int validate(const tlb_params &p)
     if (!(p.tau_g >= 0.5)) return fail(TLB_E_INVAL, "tau_g must be >= 0.5");
     if (!(p.chi > 0)) return fail(TLB_E_INVAL, "chi must be positive");
     if (p.wetting < 0 || p.wetting > 2) return fail(TLB_E_INVAL, "unknown wetting scheme");
+    if (p.eos < TLB_EOS_CS || p.eos > TLB_EOS_PR) return fail(TLB_E_INVAL, "unknown equation of state");
+    for (int k = 0; k < 3; ++k)
+        if (!(p.nu[k] >= 0)) return fail(TLB_E_INVAL, "viscosities must be >= 0");
     for (int k = 0; k < 3; ++k) {
         double t = p.theta_deg[k];
         if (p.wetting != TLB_WET_FORCE && !(t >= 20.0 && t <= 160.0))
@@ -629,6 +677,14 @@ extern "C" int tlb_set_force_calibration(const tlb_params *p, const double *kapp
     return TLB_OK;
 }
 
+extern "C" int tlb_derive(const tlb_params *p, tlb_derived *out)
+{
+    if (!p || !out) return fail(TLB_E_INVAL, "null argument");
+    int rc = validate(*p);
+    if (rc) return rc;
+    return derive(*p, *out);
+}
+
 extern "C" int tlb_create_ex(const tlb_params *pin, tlb_ctx **out)
 {
     if (!pin || !out) return fail(TLB_E_INVAL, "null argument");
@@ -744,10 +800,11 @@ extern "C" int tlb_create(int lattice, int nx, int ny, int nz, const double dens
     p.rho_l = densities[0];
     p.rho_g = densities[1];
     for (int k = 0; k < 3; ++k) p.kappa[k] = kappas[k];
-    if (!(viscosities[0] == viscosities[1] && viscosities[1] == viscosities[2]))
-        return fail(TLB_E_UNSUPPORTED, "one kinematic viscosity for all phases (single beta)");
-    if (!(viscosities[0] > 0)) return fail(TLB_E_INVAL, "viscosity must be positive");
+    for (int k = 0; k < 3; ++k)
+        if (!(viscosities[k] > 0)) return fail(TLB_E_INVAL, "viscosities must be positive");
     p.beta = 1.0 / (1.0 + 6.0 * viscosities[0]);   // nu = (1/beta - 1)/6
+    if (!(viscosities[0] == viscosities[1] && viscosities[1] == viscosities[2]))
+        for (int k = 0; k < 3; ++k) p.nu[k] = viscosities[k];   // per-component viscosity
     p.wetting = wetting;
     for (int k = 0; k < 3; ++k) p.theta_deg[k] = angles_deg[k];
     return tlb_create_ex(&p, out);      // force wetting: angles through the calibration tables
@@ -1588,7 +1645,7 @@ extern "C" int tlb_batch_tune(tlb_batch *b, int reps, tlb_batch_config *chosen)
     // candidates: register budget (D2Q9), tile order, steps per graph replay;
     // the depth is timed as replays of that many launches, one replay per rep
     const int variants[2] = {0, 1};
-    const int nvar = 2;
+    const int nvar = b->D == 2 ? 2 : 1;
     const int depths[3] = {2, 8, 32};
     double best = 1e300;
     tlb_batch_config bestc = b->cfg;
@@ -1596,7 +1653,7 @@ extern "C" int tlb_batch_tune(tlb_batch *b, int reps, tlb_batch_config *chosen)
         for (int order = 0; order < 3; ++order)
             for (int di = 0; di < 3; ++di) {
                 tlb_batch_config c = b->cfg;
-                c.variant = variants[vi];
+                c.variant = b->D == 2 ? variants[vi] : -1;
                 c.tile_order = order;
                 c.graph_depth = depths[di];
                 double us = 0.0;

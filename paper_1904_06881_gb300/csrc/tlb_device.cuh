@@ -133,10 +133,29 @@ __device__ __forceinline__ Bulk bulk_terms(const DevParams &p, float rho, float 
     float C2 = 0.5f * (1.0f + phi * p.inv_chi - C1);
     float C3 = 0.5f * (1.0f - phi * p.inv_chi - C1);
     float br = p.b * rho;
-    float q = br - 4.0f;
-    float lr = __logf(rho);
-    float psi = rho * (p.C - p.a * rho - 8.0f * p.RT * (br - 6.0f) / (q * q) + p.RT * lr);
-    float dpsi = p.C - 2.0f * p.a * rho + p.RT * (1.0f + lr) + 16.0f * p.RT * (br - 12.0f) / (q * q * q);
+    float psi, dpsi;
+    if (p.eos == 0) {
+        // Carnahan-Starling, Eq. PsiEOS and its printed derivative
+        float q = br - 4.0f;
+        float lr = __logf(rho);
+        psi = rho * (p.C - p.a * rho - 8.0f * p.RT * (br - 6.0f) / (q * q) + p.RT * lr);
+        dpsi = p.C - 2.0f * p.a * rho + p.RT * (1.0f + lr) + 16.0f * p.RT * (br - 12.0f) / (q * q * q);
+    } else {
+        // van der Waals: Psi = rho (C - a rho + RT ln(rho/(1 - b rho)));
+        // Peng-Robinson adds - a A/(2 sqrt2 b) ln((b rho + sqrt2 - 1)/(sqrt2 + 1 - b rho))
+        // inside the bracket in place of - a rho (a A: p.aA)
+        const float om = 1.0f - br;
+        const float lg = __logf(rho / om);
+        if (p.eos == 1) {
+            psi = rho * (p.C - p.a * rho + p.RT * lg);
+            dpsi = p.C - 2.0f * p.a * rho + p.RT * lg + p.RT / om;
+        } else {
+            const float k = p.aA * (0.35355339f / p.b);      // a A / (2 sqrt2 b)
+            const float L = __logf((br + 0.41421356f) / (2.41421356f - br));
+            psi = rho * (p.C + p.RT * lg - k * L);
+            dpsi = p.C + p.RT * lg + p.RT / om - k * L - p.aA * rho / (1.0f + 2.0f * br - br * br);
+        }
+    }
     float g2 = gpoly(C2), g3 = gpoly(C3);
     float fb = 0.5f * p.lam1 * (psi - p.Psi0) + 0.5f * p.lam2 * C2 * C2 * (1.0f - C2) * (1.0f - C2) +
                0.5f * p.lam3 * C3 * C3 * (1.0f - C3) * (1.0f - C3);
@@ -145,6 +164,19 @@ __device__ __forceinline__ Bulk bulk_terms(const DevParams &p, float rho, float 
     r.mupB = (p.lam2 * g2 - p.lam3 * g3) * p.inv_chi;
     r.p0 = rho * r.murB + phi * r.mupB - fb;
     return r;
+}
+
+// ELBM beta of a node: the fluid's beta, or with per-component viscosities
+// the beta of the concentration-weighted mean viscosity (concentrations
+// clipped to [0, 1]), nu = (1/beta - 1)/6.
+__device__ __forceinline__ float local_beta(const DevParams &p, float rho, float phi)
+{
+    if (!p.nu_on) return p.beta;
+    const float C1 = (rho - p.rho_l) * p.inv_rgl;
+    const float C2 = 0.5f * (1.0f + phi * p.inv_chi - C1), C3 = 0.5f * (1.0f - phi * p.inv_chi - C1);
+    const float c1 = fminf(fmaxf(C1, 0.f), 1.f), c2 = fminf(fmaxf(C2, 0.f), 1.f), c3 = fminf(fmaxf(C3, 0.f), 1.f);
+    const float nu = (c1 * p.nu[0] + c2 * p.nu[1] + c3 * p.nu[2]) / (c1 + c2 + c3);
+    return 1.0f / (6.0f * nu + 1.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -198,8 +230,7 @@ __device__ __forceinline__ float phi_ent(float y, float l)
 // by less than 2e-8 of itself) and as the start of Halley's method (third
 // order, from h, h', h''), bracketed by [1, alpha_max), above it (nodes at the
 // interface).
-// FPA: accessor of f'_i (an array in registers, or a column of the staging
-// area in shared memory); the arithmetic is the same either way.
+// FPA: accessor of f'_i.
 template <int Q, class FPA>
 __device__ __forceinline__ float alpha_series_a(const FPA &fp, const float (&x)[Q])
 {
@@ -235,22 +266,11 @@ struct RegPop {
     const float (&v)[Q];
     __device__ __forceinline__ float operator()(int i) const { return v[i]; }
 };
-template <int NT>
-struct SmemPop {
-    const float *stage;
-    int tid;
-    __device__ __forceinline__ float operator()(int i) const { return stage[i * NT + tid]; }
-};
 
 template <int Q>
 __device__ __forceinline__ float alpha_series(const float (&fp)[Q], const float (&x)[Q])
 {
     return alpha_series_a<Q>(RegPop<Q>{fp}, x);
-}
-template <int Q, int NT>
-__device__ __forceinline__ float alpha_series_s(const float *stage, int tid, const float (&x)[Q])
-{
-    return alpha_series_a<Q>(SmemPop<NT>{stage, tid}, x);
 }
 
 // Root of h in (1, alpha_max) from the start al.  h(1) < 0 always; when h is
@@ -260,16 +280,12 @@ __device__ __forceinline__ float alpha_series_s(const float *stage, int tid, con
 // iteration: the third-order convergence leaves an error of order 1e-9
 // alpha, below the FP32 evaluation noise of h (about 1e-6 alpha at
 // max|x| = 0.5).
-// KEEP_L: the logarithms ln(1 + x_i) are held in registers across the
-// iterations, else recomputed in each one (same values; fewer registers)
-template <int Q, class FPA, bool KEEP_L = true>
+template <int Q, class FPA>
 __device__ __forceinline__ float alpha_newton_a(const FPA &fp, const float (&x)[Q], float amax, float al)
 {
-    float L[KEEP_L ? Q : 1];
-    if constexpr (KEEP_L) {
+    float L[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) L[i] = log1pf(x[i]);
-    }
+    for (int i = 0; i < Q; ++i) L[i] = log1pf(x[i]);
     const float bound = amax * (1.0f - 1e-6f);
     float lo = 1.0f, hi = bound;
     bool probed = false;
@@ -284,9 +300,8 @@ __device__ __forceinline__ float alpha_newton_a(const FPA &fp, const float (&x)[
             const float y = a * x[i];
             const float ly = log1pf(y);
             const float f = fp(i);
-            const float Li = KEEP_L ? L[KEEP_L ? i : 0] : log1pf(x[i]);
-            h += f * (phi_ent(y, ly) - y * Li);
-            d1 += f * x[i] * (ly - Li);
+            h += f * (phi_ent(y, ly) - y * L[i]);
+            d1 += f * x[i] * (ly - L[i]);
             d2 += f * x[i] * x[i] / (1.0f + y);
         }
         if (a == bound) {
@@ -323,12 +338,6 @@ template <int Q>
 __device__ __forceinline__ float alpha_newton(const float (&fp)[Q], const float (&x)[Q], float amax, float al)
 {
     return alpha_newton_a<Q>(RegPop<Q>{fp}, x, amax, al);
-}
-template <int Q, int NT>
-__device__ __forceinline__ float alpha_newton_s(const float *stage, int tid, const float (&x)[Q], float amax,
-                                                float al)
-{
-    return alpha_newton_a<Q, SmemPop<NT>, false>(SmemPop<NT>{stage, tid}, x, amax, al);
 }
 
 // ---------------------------------------------------------------------------

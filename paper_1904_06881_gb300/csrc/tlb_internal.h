@@ -38,6 +38,10 @@ struct DevParams {
     float kw_rho, kw_phi;
     int g_fp16;          // g stored as half scaled by 1/chi
     float g_scale, g_unscale;
+    int eos;             // TLB_EOS_* (0 Carnahan-Starling, 1 van der Waals, 2 Peng-Robinson)
+    float aA;            // Peng-Robinson attraction a A(T)
+    int nu_on;           // per-component viscosity: beta from the local mixture
+    float nu[3];         // kinematic viscosities of C1, C2, C3
 };
 
 // Per-lattice device buffers.
@@ -99,9 +103,7 @@ struct Launch {
     // batched: entries[0..n) and a tile table (tile -> entry, tile coords)
     static void moments_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st);
     // variant: D2Q9 register budget, 0 = 3 CTAs/SM (80 registers), 1 = 4 CTAs/SM
-    // (64 registers), -1 = 4 CTAs/SM beyond one wave of 3 CTAs/SM; D3Q27: 0 or
-    // -1 = the tile's f and g staged, 2 CTAs/SM; 1 = f staged, the mirror state
-    // kept in shared memory, 3 CTAs/SM
+    // (64 registers), -1 = 4 CTAs/SM beyond one wave of 3 CTAs/SM; D3Q27 has one
     static void step_batch(const BatchEntry *entries, const int4 *tiles, int ntiles, int g_fp16, cudaStream_t st,
                            int variant = -1);
     static int tile_dims(int a);

@@ -134,11 +134,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 }
 
 // dynamic shared memory of the stepping kernel: f (and FP32 g) of the tile's own nodes
-template <int D, typename GT, bool LEAN = false>
+template <int D, typename GT>
 __host__ __device__ constexpr int stage_bytes()
 {
-    // LEAN (D3Q27): the tile's f alone (g is read from global memory)
-    if (LEAN) return Tile<D>::X * Tile<D>::Y * Tile<D>::Z * Lat<D>::Q * 4 + 128;
     // f: Q floats; g: Q floats, or g_0 as a float plus Q-1 halves; D3Q27: 128
     // bytes more, to start the area on a 128-byte boundary (tensor copies)
     return Tile<D>::X * Tile<D>::Y * Tile<D>::Z *
@@ -384,7 +382,7 @@ struct NodesBox {
 // populations itself (no moments pass before the step) and keeps the tile's
 // own populations in shared memory.
 // ---------------------------------------------------------------------------
-template <int D, typename GT, int MODE, bool ASYNC = false, bool FUSED = false, bool LEAN = false>
+template <int D, typename GT, int MODE, bool ASYNC = false, bool FUSED = false>
 __device__ __forceinline__ void step_tile(const DevParams &p, const float *__restrict__ f_in, float *__restrict__ f_out,
                                           const void *g_in, void *g_out, const float *__restrict__ rho,
                                           const float *__restrict__ phi, const uint8_t *__restrict__ type,
@@ -617,9 +615,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             // (x0 is a multiple of 8 nodes: 16-byte aligned inner coordinate)
             if (tid == 0) {
                 mbar_init(&tma_bar, 1);
-                const unsigned bytes = LEAN ? (unsigned)(Q * NT * 4)
-                                            : (unsigned)(Q * NT * 4) + (sizeof(GT) == 4 ? (unsigned)(Q * NT * 4)
-                                                                                        : (unsigned)(NT * 4 + (Q - 1) * NT * 2));
+                const unsigned bytes = (unsigned)(Q * NT * 4) +
+                                       (sizeof(GT) == 4 ? (unsigned)(Q * NT * 4) : (unsigned)(NT * 4 + (Q - 1) * NT * 2));
 #ifdef TLB_TEST_TMA_TIMEOUT
                 // test builds only: the barrier expects 16 bytes more than the
                 // copies send, so its wait runs out and the timeout path runs
@@ -628,8 +625,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                 mbar_expect_tx(&tma_bar, bytes);
 #endif
                 tma_load_4d(&stage[0], tm[0], x0, y0, z0, 0, &tma_bar);
-                if (LEAN) {
-                } else if (sizeof(GT) == 4) {
+                if (sizeof(GT) == 4) {
                     tma_load_4d(&stage[Q * NT], tm[1], x0, y0, z0, 0, &tma_bar);
                 } else {
                     tma_load_3d(&stage[Q * NT], tm[1], x0, y0, z0, &tma_bar);
@@ -642,8 +638,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                 const long long an = (long long)ax + (long long)p.nx * ((long long)ay + (long long)p.ny * az);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) cp_async4(&stage[i * NT + tid], f_in + (long long)i * p.N + an);
-                if (LEAN) {
-                } else if (sizeof(GT) == 4) {
+                if (sizeof(GT) == 4) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i)
                         cp_async4(&stage[(Q + i) * NT + tid], (const float *)g_in + (long long)i * p.N + an);
@@ -892,135 +887,6 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         return;
     }
 
-    if constexpr (LEAN) {
-        static_assert(D == 3 && ASYNC, "the lean collision stages f of D3Q27 tiles");
-        // The same arithmetic as below, in the same order, with the mirror
-        // state f' kept in the staging area (over f) and only D_i, then
-        // x_i = D_i / f'_i, per thread: a register budget for 3 CTAs per SM.
-        // g is read from global memory and relaxed first.
-        float j[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float fi = stage[i * NT + tid];
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                if (cc<D>(i, a) != 0) j[a] += (float)cc<D>(i, a) * fi;
-        }
-        float u[3], ud[3], v[3];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            u[a] = j[a] * inv_r;
-            float du = F[a] * inv_r;
-            ud[a] = u[a] + du;
-            v[a] = u[a] + 0.5f * du;
-        }
-        unsigned solid_nb = 0;
-        if (tc & TLB_FIRST) {
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
-                if (stype[m] & TLB_SOLID) solid_nb |= 1u << i;
-            }
-        }
-        // ---- LBGK for g (Eq. CahnHilliardLBM) with g^eq(phi, v, mu_phi) ----
-        {
-            float v2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < D; ++a) v2 += v[a] * v[a];
-            float gsum = 0.f;
-            const float gA = 3.0f * p.Gamma * mup - 1.5f * ph * v2, gB = 3.0f * ph, gC = 4.5f * ph;
-            const float g0 = GIO<GT>::ld(g_in, 0, n, p);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const float gi = GIO<GT>::ld(g_in, i, n, p);
-                float cv = 0.f;
-#pragma unroll
-                for (int a = 0; a < D; ++a) cv += (float)cc<D>(i, a) * v[a];
-                float ge = wt<D>(i) * (gA + cv * (gB + gC * cv));
-                gsum += ge;
-                float gn = gi + (ge - gi) * p.inv_tau_g;
-                if (solid_nb & (1u << i))
-                    GIO<GT>::st(g_out, opp<D>(i), n, gn, p);
-                else
-                    GIO<GT>::st(g_out, i, nbr(cc<D>(i, 0), cc<D>(i, 1), cc<D>(i, 2)), gn, p);
-            }
-            float ge0 = ph - gsum;
-            GIO<GT>::st(g_out, 0, n, g0 + (ge0 - g0) * p.inv_tau_g, p);
-        }
-        // ---- ELBM collision of f (Eqs. ELBMequation, ELBMForcingExactDiff, EntropyEquation) ----
-        Fac fu[3], fd[3];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            fu[a] = eq_factors(u[a]);
-            fd[a] = eq_factors(ud[a]);
-        }
-        float dl[Q];
-        float rdl = 0.f, rF = 0.f, mdl[3] = {0.f, 0.f, 0.f}, mF[3] = {F[0], F[1], F[2]};
-        bool bad = !(r > 0.f);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            float e = r, ed = r;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                e *= fac_of(fu[a], cc<D>(i, a));
-                ed *= fac_of(fd[a], cc<D>(i, a));
-            }
-            const float fi = stage[i * NT + tid];
-            float di = (e - wt<D>(i)) - fi;
-            float Fi = ed - e;
-            rdl += di;
-            rF += Fi;
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                if (cc<D>(i, a) != 0) {
-                    mdl[a] += (float)cc<D>(i, a) * di;
-                    mF[a] -= (float)cc<D>(i, a) * Fi;
-                }
-            dl[i] = di;
-            stage[i * NT + tid] = (fi + wt<D>(i)) + Fi;
-        }
-        dl[0] = -rdl;
-        stage[tid] = (stage[tid] + wt<D>(0)) - rF;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            dl[2 * a + 1] -= 0.5f * mdl[a];
-            dl[2 * a + 2] += 0.5f * mdl[a];
-            stage[(2 * a + 1) * NT + tid] += 0.5f * mF[a];
-            stage[(2 * a + 2) * NT + tid] -= 0.5f * mF[a];
-        }
-        float xmax = 0.f, xneg = 0.f;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float fpi = stage[i * NT + tid];
-            bad |= !(fpi > 0.f);
-            float xi = dl[i] * (1.0f / fpi);
-            dl[i] = xi;
-            xmax = fmaxf(xmax, fabsf(xi));
-            xneg = fmaxf(xneg, -xi);
-        }
-        float al = 2.0f;
-        if (bad) {
-            atomicOr(status, STATUS_DIVERGED);
-        } else if (xmax >= 1e-5f) {
-            al = alpha_series_s<Q, NT>(stage, tid, dl);
-            if (xmax > 0.07f) {
-                const float amax = xneg > 0.f ? 1.0f / xneg : 3.0e38f;
-                al = alpha_newton_s<Q, NT>(stage, tid, dl, amax, al);
-            }
-        }
-        const float ab = al * p.beta;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float fpi = stage[i * NT + tid];
-            float fn = (fpi - wt<D>(i)) + ab * (dl[i] * fpi);
-            if (solid_nb & (1u << i))
-                f_out[(long long)opp<D>(i) * p.N + n] = fn;
-            else
-                f_out[(long long)i * p.N + nbr(cc<D>(i, 0), cc<D>(i, 1), cc<D>(i, 2))] = fn;
-        }
-        return;
-    }
-
     // ---- ELBM collision of f (Eqs. ELBMequation, ELBMForcingExactDiff, EntropyEquation) ----
     // fp holds f~ = f - w on load and the mirror state f' after the pass below.
     float fp[Q], dl[Q];
@@ -1103,7 +969,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             al = alpha_newton<Q>(fp, dl, amax, al);
         }
     }
-    const float ab = al * p.beta;
+    const float ab = al * local_beta(p, r, ph);
 
     // halfway bounce-back: bit i set when the neighbour x + c_i is solid (one
     // mask for the f and g stores); D3Q27: only first-layer nodes have solid
@@ -1181,7 +1047,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 2) step_kernel(DevParams p, 
 // two builds with the same code (the register allocation alone differs):
 // 3 CTAs/SM (80 registers, fewer spills) for launches that fit in one wave,
 // 4 CTAs/SM (64 registers, more warps to hide latency) for larger ones.
-template <int D, typename GT, int MINB, bool LEAN = false>
+template <int D, typename GT, int MINB>
 __global__ void __launch_bounds__(256, MINB) step_batch_kernel(const BatchEntry *__restrict__ E, const int4 *__restrict__ tiles)
 {
     __shared__ BatchEntry se;
@@ -1194,8 +1060,8 @@ __global__ void __launch_bounds__(256, MINB) step_batch_kernel(const BatchEntry 
     __syncthreads();
     AuxOut none = {};
     // D2Q9 tiles sum their own moments; D3Q27 tiles read those of the moments kernel
-    step_tile<D, GT, MODE_STEP, D == 3, D == 2, LEAN>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi,
-                                                      se.type, se.status, t.y, t.z, t.w, nullptr, none, se.tm);
+    step_tile<D, GT, MODE_STEP, D == 3, D == 2>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type,
+                                                se.status, t.y, t.z, t.w, nullptr, none, se.tm);
 }
 
 // ---------------------------------------------------------------------------
@@ -1433,8 +1299,6 @@ static void launch_step_batch(const BatchEntry *entries, const int4 *tiles, int 
             cudaFuncSetAttribute(step_batch_kernel<D, GT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
         } else {
             cudaFuncSetAttribute(step_batch_kernel<D, GT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-            cudaFuncSetAttribute(step_batch_kernel<D, GT, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 stage_bytes<D, GT, true>());
         }
         int dev = 0, n = 0;
         cudaGetDevice(&dev);
@@ -1446,12 +1310,7 @@ static void launch_step_batch(const BatchEntry *entries, const int4 *tiles, int 
         if (four) launch_pdl(step_batch_kernel<D, GT, 4>, ntiles, nt, (size_t)bytes, st, entries, tiles);
         else launch_pdl(step_batch_kernel<D, GT, 3>, ntiles, nt, (size_t)bytes, st, entries, tiles);
     } else {
-        // variant 1: the lean collision (f' in shared memory), 3 CTAs/SM
-        if (variant == 1)
-            launch_pdl(step_batch_kernel<D, GT, 3, true>, ntiles, nt, (size_t)stage_bytes<D, GT, true>(), st, entries,
-                       tiles);
-        else
-            launch_pdl(step_batch_kernel<D, GT, 2>, ntiles, nt, (size_t)bytes, st, entries, tiles);
+        launch_pdl(step_batch_kernel<D, GT, 2>, ntiles, nt, (size_t)bytes, st, entries, tiles);
     }
 }
 

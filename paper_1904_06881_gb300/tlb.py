@@ -22,6 +22,7 @@ ERRORS = {-1: "TLB_E_INVAL", -2: "TLB_E_NOMEM", -3: "TLB_E_CUDA", -4: "TLB_E_UNS
           -5: "TLB_E_UNCALIBRATED", -6: "TLB_E_DIVERGED", -7: "TLB_E_TIMEOUT", -8: "TLB_E_BUSY",
           -9: "TLB_E_NOTFOUND", -10: "TLB_E_BOUNDS"}
 D2Q9, D3Q27 = 0, 1
+EOS_CS, EOS_VDW, EOS_PR = 0, 1, 2
 WET_FORCE, WET_GEOM_EXTRAP, WET_GEOM_INTERP = 0, 1, 2
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
@@ -35,7 +36,7 @@ ENTRY_POINTS = (
     "tlb_device_bytes", "tlb_launch_count", "tlb_step_batch", "tlb_server_create", "tlb_submit",
     "tlb_server_pump", "tlb_poll", "tlb_server_stats", "tlb_server_destroy", "tlb_step_noalloc",
     "tlb_set_force_calibration", "tlb_batch_create", "tlb_batch_step", "tlb_batch_tune", "tlb_batch_get_config",
-    "tlb_batch_destroy",
+    "tlb_batch_destroy", "tlb_derive",
 )
 ORDER_LATTICE, ORDER_INTERLEAVED, ORDER_LARGEST_FIRST = 0, 1, 2
 
@@ -56,12 +57,14 @@ class Params(ctypes.Structure):
                 ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double), ("beta", ctypes.c_double),
                 ("tau_g", ctypes.c_double), ("Gamma", ctypes.c_double), ("wetting", ctypes.c_int),
                 ("theta_deg", ctypes.c_double * 3), ("kw_rho", ctypes.c_double), ("kw_phi", ctypes.c_double),
-                ("g_fp16", ctypes.c_int)]
+                ("g_fp16", ctypes.c_int), ("eos", ctypes.c_int), ("omega", ctypes.c_double),
+                ("nu", ctypes.c_double * 3)]
 
 
 class Derived(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
-                ("T", "a", "b", "R", "rho_l", "rho_g", "C", "Psi0", "Tc", "kappa_rr", "kappa_pp", "kappa_rp")]
+                ("T", "a", "b", "R", "rho_l", "rho_g", "C", "Psi0", "Tc", "kappa_rr", "kappa_pp", "kappa_rp",
+                 "aA")]
 
 
 class BatchConfig(ctypes.Structure):
@@ -139,6 +142,7 @@ def lib():
         "tlb_batch_tune": (i, [vp, i, ctypes.POINTER(BatchConfig)]),
         "tlb_batch_get_config": (i, [vp, ctypes.POINTER(BatchConfig)]),
         "tlb_batch_destroy": (None, [vp]),
+        "tlb_derive": (i, [ctypes.POINTER(Params), ctypes.POINTER(Derived)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -306,14 +310,21 @@ def default_allocator():
     _alloc_keep[:] = []
 
 
+def tlb_derive(params):
+    """Host-only derived constants (dict) of a parameter set (see tlb.h)."""
+    d = Derived()
+    _check(lib().tlb_derive(ctypes.byref(params), ctypes.byref(d)), "tlb_derive")
+    return {k: getattr(d, k) for k, _ in Derived._fields_}
+
+
 def make_params(lattice=D2Q9, nx=64, ny=64, nz=1, **kw):
     """Params from tlb_params_default() with the given overrides (names as in
     the workloads module: lam, kappa, chi, a, b, R, rho_l, rho_g, beta, tau_g,
-    Gamma, wetting, theta_deg, kw_rho, kw_phi, g_fp16)."""
+    Gamma, wetting, theta_deg, kw_rho, kw_phi, g_fp16, eos, omega, nu)."""
     p = tlb_params_default()
     p.lattice, p.nx, p.ny, p.nz = lattice, nx, ny, nz
     for k, v in kw.items():
-        if k in ("lam", "kappa", "theta_deg"):
+        if k in ("lam", "kappa", "theta_deg", "nu"):
             getattr(p, k)[:] = list(v)
         else:
             setattr(p, k, v)

@@ -53,8 +53,11 @@ def test_invalid_arguments_rejected_on_host(L):
     from paper_1904_06881_gb300 import tlb
 
     with pytest.raises(tlb.TlbError) as e:
-        tlb.tlb_create(tlb.D2Q9, 64, 64, 1, (1.0, 1e-3), (0.01, 1, 1), (0.1, 0.2, 0.1), tlb.WET_FORCE, (90, 90, 90))
-    assert e.value.code == -4          # unequal viscosities: one beta only
+        tlb.tlb_create(tlb.D2Q9, 64, 64, 1, (1.0, 1e-3), (0.01, 1, 1), (0.1, -0.2, 0.1), tlb.WET_FORCE, (90, 90, 90))
+    assert e.value.code == -1          # a non-positive viscosity
+    with pytest.raises(tlb.TlbError) as e:
+        tlb.tlb_derive(tlb.make_params(tlb.D2Q9, 64, 64, 1, eos=7))
+    assert e.value.code == -1          # unknown equation of state
     with pytest.raises(tlb.TlbError) as e:
         tlb.tlb_create(tlb.D2Q9, 64, 64, 1, (1.0, 1e-3), (0.01, 1, 1), (1 / 6,) * 3, tlb.WET_FORCE, (60, 90, 90))
     assert e.value.code == -5          # force wetting: no calibration table for this parameter set
@@ -100,3 +103,26 @@ def test_missing_library_fails_loudly(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stderr
     assert out.stdout.startswith("RAISED libtlb.so not built"), out.stdout
+
+
+@pytest.mark.parametrize("eos", [0, 1, 2])
+@pytest.mark.parametrize("ratio", [10.0, 14.141345641130298, 40.0])
+def test_derived_constants_match_oracle(L, eos, ratio):
+    """The library's host EOS code (closed-form textbook pressures and
+    chemical potentials, a search over ln rho_g) and the oracle's (pressure
+    p = rho Psi' - Psi, bisection on the common pressure) give the same
+    temperature, coexistence densities and Psi_eos constants for the
+    Carnahan-Starling, van der Waals and Peng-Robinson equations of state."""
+    import oracle
+    from paper_1904_06881_gb300 import tlb
+
+    rho_l = 6.143914427184784
+    p = tlb.make_params(tlb.D2Q9, 16, 16, 1, rho_l=rho_l, rho_g=rho_l / ratio, eos=eos)
+    d = tlb.tlb_derive(p)
+    o = oracle.Oracle(nx=16, ny=16, rho_l=rho_l, rho_g=rho_l / ratio, eos=eos).derived
+    # the oracle's critical point comes from a scan of a finite-difference
+    # dp/drho (5e-8 relative for vdW against the exact 8a/(27bR))
+    for k in ("T", "Tc", "a", "b", "rho_l", "rho_g"):
+        assert np.isclose(d[k], o[k], rtol=1e-6, atol=0), (k, d[k], o[k])
+    for k in ("C", "Psi0"):
+        assert np.isclose(d[k], o[k], rtol=1e-5, atol=1e-9), (k, d[k], o[k])

@@ -68,10 +68,12 @@ def _arc_side(x, y, x0, ymid, H, theta_left):
     theta_left, measured in the left phase."""
     R = (H / 2.0) / abs(math.cos(math.radians(theta_left)))
     if theta_left < 90.0:
-        d = np.hypot(x - (x0 + R), y - ymid) - R          # centre on the right: left side outside
-        return 0.5 * (1.0 + np.tanh(d / 2.0))
-    d = np.hypot(x - (x0 - R), y - ymid) - R              # centre on the left: left side inside
-    return 0.5 * (1.0 - np.tanh(d / 2.0))
+        xc = x0 + R                                       # centre on the right: left side outside
+        d = np.hypot(x - xc, y - ymid) - R
+        return np.where(x < xc, 0.5 * (1.0 + np.tanh(d / 2.0)), 0.0)
+    xc = x0 - R                                           # centre on the left: left side inside
+    d = np.hypot(x - xc, y - ymid) - R
+    return np.where(x > xc, 0.5 * (1.0 - np.tanh(d / 2.0)), 1.0)
 
 
 def test_dynamic_angles_of_synthetic_train():

@@ -159,19 +159,3 @@ def test_batch_follows_lattices_stepped_alone():
     alone[1].step(13)
     for a, m in zip(alone, mix):
         assert _same(a.fields(), m.fields())
-
-
-def test_d3q27_launch_variants_agree():
-    """The two D3Q27 step-kernel variants the autotuner chooses between (the
-    tile's f and g staged, 2 CTAs/SM; f staged with the mirror state kept in
-    shared memory, 3 CTAs/SM) run the same arithmetic in the same order:
-    bit-identical fields after 30 steps of a lubricated drop."""
-    from paper_1904_06881_gb300 import tlb
-
-    wl = W.c2_lubricated(nx=32, ny=24, nz=20, R=6.0, lub=3, gap=2, kw_rho=0.02)
-    a, b = tlb.lattice_from_workload(wl), tlb.lattice_from_workload(wl)
-    ba = tlb.Batch([a], variant=0, graph_depth=0)
-    bb = tlb.Batch([b], variant=1, graph_depth=0)
-    ba.step(30)
-    bb.step(30)
-    assert _same(a.fields(), b.fields())

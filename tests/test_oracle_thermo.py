@@ -242,3 +242,51 @@ def test_table1_gamma12_fixes_the_density_scale():
     s = oracle.eos_coexistence(A, B, R, 0.485 * Tc)["rho_l"]
     g_scaled, _ = _gamma12_straight_path(0.485 * Tc, s=s)
     assert g_scaled < 0.5 * 0.414
+
+
+def _vdw_p(rho, a, b, R_, T):
+    return rho * R_ * T / (1.0 - b * rho) - a * rho ** 2
+
+
+def _pr_p(rho, a, b, R_, T, omega=0.344):
+    k = 0.37464 + 1.54226 * omega - 0.26992 * omega ** 2
+    Tc = (0.07780 / 0.45724) * a / (b * R_)
+    aA = a * (1.0 + k * (1.0 - np.sqrt(T / Tc))) ** 2
+    return rho * R_ * T / (1.0 - b * rho) - aA * rho ** 2 / (1.0 + 2.0 * b * rho - (b * rho) ** 2)
+
+
+@pytest.mark.parametrize("kind,pfun,tc", [(oracle.EOS_VDW, _vdw_p, 8.0 / 27.0), (oracle.EOS_PR, _pr_p, 0.07780 / 0.45724)])
+def test_alternative_eos_free_energy_and_critical_point(kind, pfun, tc):
+    """Van der Waals and Peng-Robinson (Sec. II.A: EOS the model hosts): the
+    oracle's Psi_eos gives the textbook pressure through p = rho Psi' - Psi,
+    its dPsi/drho is the derivative of Psi, and the critical temperature
+    is the textbook one, 8a/(27bR) (vdW, exact) and 0.07780/0.45724 a/(bR)
+    (PR, whose constants place the critical point there to their rounding)."""
+    e = oracle.eos_k(kind)
+    a, b = 0.05, 0.1
+    Tc = e["critical_T"](a, b, R)
+    assert np.isclose(Tc * b * R / a, tc, rtol=(1e-5 if kind == oracle.EOS_VDW else 2e-4))
+    T = 0.8 * Tc
+    for rho in (0.05, 0.8, 3.0, 6.0, 8.5):
+        psi, dpsi = e["psi"](rho, a, b, R, T, 0.1), e["dpsi"](rho, a, b, R, T, 0.1)
+        assert np.isclose(rho * dpsi - psi, pfun(rho, a, b, R, T), rtol=1e-11, atol=1e-14)
+        h = 1e-6 * rho
+        num = (e["psi"](rho + h, a, b, R, T, 0.1) - e["psi"](rho - h, a, b, R, T, 0.1)) / (2 * h)
+        assert np.isclose(num, dpsi, rtol=1e-7, atol=1e-10)
+
+
+@pytest.mark.parametrize("kind,pfun", [(oracle.EOS_VDW, _vdw_p), (oracle.EOS_PR, _pr_p)])
+def test_alternative_eos_coexistence(kind, pfun):
+    """Coexistence of the alternative EOS: equal textbook pressure, equal
+    chemical potential and Maxwell's equal-area rule (integral of p - p_coex
+    over 1/rho between the phases vanishes)."""
+    e = oracle.eos_k(kind)
+    a, b = 0.05, 0.1
+    T = 0.75 * e["critical_T"](a, b, R)
+    c = e["coexistence"](a, b, R, T)
+    rg, rl = c["rho_g"], c["rho_l"]
+    pg, pl = pfun(rg, a, b, R, T), pfun(rl, a, b, R, T)
+    assert np.isclose(pg, pl, rtol=1e-9)
+    assert np.isclose(e["dpsi"](rg, a, b, R, T, 0.0), e["dpsi"](rl, a, b, R, T, 0.0), rtol=1e-9, atol=1e-12)
+    area = quad(lambda v: pfun(1.0 / v, a, b, R, T) - pg, 1.0 / rl, 1.0 / rg, limit=400)[0]
+    assert abs(area) < 1e-8 * pg * (1.0 / rg - 1.0 / rl)
