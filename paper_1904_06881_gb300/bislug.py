@@ -203,6 +203,39 @@ def slip_length(thetas_deg, cas, theta_w_deg, lam, Lc):
     return Lc * math.exp(-m), m
 
 
+# the three interfaces of a train moving towards +x: the angle key (Sec. IV
+# convention), the phase it is measured in, and the advancing and receding
+# components (0 gas, 1 C2, 2 C3)
+INTERFACES = (("theta_21", "rear gas | C2", 0, 1), ("theta_23", "C2 | C3", 1, 2), ("theta_31", "front C3 | gas", 2, 0))
+
+
+def cox_slip(runs, gammas, rho, nu=1.0 / 6.0, Lc=39.0):
+    """Slip lengths of Sec. VI from steady trains of one angle set at several
+    speeds.  runs: [(v_inf, dynamic_angles dict)], gammas = (g12, g13, g23),
+    rho = (rho_gas, rho_C2, rho_C3).  Per interface: the static angle theta_w
+    is the intercept at zero speed of a straight line through theta(v) (Sec.
+    VI: the angles vary linearly with the speed); Cox's relation is taken in
+    the form that is invariant under relabelling the two fluids (the
+    exchange symmetry of f): theta measured in the advancing fluid, Ca = mu_adv
+    v / gamma, lambda = mu_rec / mu_adv (mu = rho nu); the slope of g(theta,
+    lambda) - g(theta_w, lambda) against Ca gives L_s = L_c exp(-m).
+    Returns {key: dict(theta_w, slope_deg_per_v, L_s, m, lam)}."""
+    gam = {"theta_21": gammas[0], "theta_23": gammas[2], "theta_31": gammas[1]}
+    out = {}
+    v = np.array([r[0] for r in runs], float)
+    for key, _, adv, rec in INTERFACES:
+        th = np.array([r[1][key] for r in runs], float)
+        # the angle in the advancing fluid: theta_21 is measured in C2, which
+        # recedes at the rear interface, so the gas's angle is its supplement
+        th_adv = 180.0 - th if key == "theta_21" else th
+        k, th0 = np.polyfit(v, th_adv, 1)
+        lam = rho[rec] / rho[adv]
+        ca = rho[adv] * nu * v / gam[key]
+        Ls, m = slip_length(th_adv, ca, th0, lam, Lc)
+        out[key] = dict(theta_w=float(th0), slope_deg_per_v=float(k), L_s=float(Ls), m=float(m), lam=float(lam))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--H", type=int, default=39)

@@ -301,9 +301,12 @@ def c4_requests(seed=4, n=256, rate=20.0, sizes_2d=(64, 128, 256, 512, 1024), si
     sessile drops (L^2, L in sizes_2d), capillary channels (nx x 64,
     nx in 256-1024), lubricated substrates (D3Q27 n^3, n in sizes_3d), liquid
     lenses and drop trains (2D); uniform random angles in [30, THETA_MAX]
-    deg; the liquid-gas density ratio log-uniform between 2 and the
+    deg; the liquid-gas density ratio log-uniform between 4 and the
     workloads' 14.1 (the gas density rho_l / ratio), or a liquid-liquid
     request (ratio 1: the gas replaced by liquid 2) in one request of eight.
+    (Below a ratio of about 3.5 the density jump is so small that the lambda_2,
+    lambda_3 wells, whose weight in mu_rho grows as 1/drho^2, give the liquid
+    a sound speed above the lattice's, and the step diverges.)
     Steps: 2D 1000-5000, 3D 500-2000.  Returns a list of (arrival_s,
     workload dict, steps)."""
     rng = np.random.default_rng(seed)
@@ -314,7 +317,7 @@ def c4_requests(seed=4, n=256, rate=20.0, sizes_2d=(64, 128, 256, 512, 1024), si
         kind = rng.choice(["drop", "channel", "lubricated", "lens", "train"], p=[0.35, 0.2, 0.1, 0.15, 0.2])
         th = float(rng.uniform(30.0, THETA_MAX))
         ll = rng.uniform() < 0.125
-        ratio = float(np.exp(rng.uniform(np.log(2.0), np.log(ratio_max))))
+        ratio = float(np.exp(rng.uniform(np.log(4.0), np.log(ratio_max))))
         if kind == "drop":
             L = int(rng.choice(sizes_2d))
             mask, rho, phi = sessile_drop_2d(L, L, L / 4.0, xc=L / 2.0, yc=0.5, rho_g=RHO_L / ratio)
