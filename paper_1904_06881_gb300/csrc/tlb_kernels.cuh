@@ -269,9 +269,6 @@ struct Thermo {
     float P[6];     // xx yy zz xy xz yz
 };
 
-template <int D>
-__device__ __forceinline__ void thermo_finish(const DevParams &p, float r0, float p0v, Thermo<D> &t);
-
 template <int D, int RX, int RY>
 __device__ __forceinline__ Thermo<D> node_thermo(const DevParams &p, const float *srho, const float *sphi, int hx,
                                                  int hy, int hz)
@@ -300,15 +297,6 @@ __device__ __forceinline__ Thermo<D> node_thermo(const DevParams &p, const float
         t.lr += 2.0f * w3 * (rm - r0);
         t.lp += 2.0f * w3 * (pm - p0v);
     }
-    thermo_finish<D>(p, r0, p0v, t);
-    return t;
-}
-
-// mu, P of a node from its rho, phi and their gradients and Laplacians (t.gr,
-// t.gp, t.lr, t.lp): Eqs. bulkchempot*, gradchempot*, pressuretensor
-template <int D>
-__device__ __forceinline__ void thermo_finish(const DevParams &p, float r0, float p0v, Thermo<D> &t)
-{
     t.b = bulk_terms(p, r0, p0v);
     t.mur = t.b.murB - p.krr * t.lr - p.krp * t.lp;
     t.mup = t.b.mupB - p.kpp * t.lp - p.krp * t.lr;
@@ -332,6 +320,7 @@ __device__ __forceinline__ void thermo_finish(const DevParams &p, float r0, floa
         }
         t.P[k] = v;
     }
+    return t;
 }
 
 template <int D>
@@ -412,22 +401,15 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     // D3Q27 per node as {xx, yy, zz, xy} and {xz, yz}, so that the force
     // stencil reads a neighbour's tensor with two vector loads
     __shared__ float sQ[D == 2 ? NC : 1][D == 2 ? NS : 1];
-    // D3Q27: sQa, sQb and smu are carved from one buffer, which first holds
-    // the z-pass sums of the separable stencils (stage B)
-    constexpr int NZP = RX * RY * SZ, NYP = RX * SY * SZ;
-    constexpr int NQBUF = (D == 3) ? (4 * NZP > 7 * NS ? 4 * NZP : 7 * NS) : 1;
-    __shared__ __align__(16) float sQbuf[NQBUF];
-    __shared__ float sYp[D == 3 ? 6 * NYP : 1];
-    float4 *const sQa = reinterpret_cast<float4 *>(sQbuf);
-    float2 *const sQb = reinterpret_cast<float2 *>(sQbuf + 4 * NS);
+    __shared__ float4 sQa[D == 3 ? NS : 1];
+    __shared__ float2 sQb[D == 3 ? NS : 1];
     // component c (qcomp order) of Q at slot m
     auto qc = [&](int c, int m) -> float {
         if constexpr (D == 2) return sQ[c][m];
         else return c == 0 ? sQa[m].x : c == 1 ? sQa[m].y : c == 2 ? sQa[m].z : c == 3 ? sQa[m].w
                     : c == 4 ? sQb[m].x : sQb[m].y;
     };
-    __shared__ float smu2[D == 3 ? 1 : NS];
-    float *const smu = D == 3 ? sQbuf + 6 * NS : smu2;
+    __shared__ float smu[NS];
     __shared__ uint8_t stype[NS];
     __shared__ uint8_t srt[NR];               // node flags of the tile + halo 2
     // FUSED tiles with ghost nodes: flags and moments of the tile + halo 2
@@ -707,38 +689,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     }
     __syncthreads();
 
-    // Stage B: Q = rho c_s^2 I - P and mu_phi at every fluid node of the tile + halo 1.
-    // D3Q27: the 26-neighbour stencils are products of one-dimensional ones
-    // (w_i = w(c_x) w(c_y) w(c_z), w(0) = 2/3, w(+-1) = 1/6): with S the
-    // smoothing (1, 4, 1)/6 and D the difference (-1, 0, 1) along an axis,
-    // grad_x q = D_x S_y S_z q / 2 (likewise y, z) and lap q = 6 (S_x S_y S_z q
-    // - q), formed in three passes over the region (z, then y, then x).
-    if constexpr (D == 3) {
-        float *const zr = sQbuf, *const zdr = sQbuf + NZP, *const zp = sQbuf + 2 * NZP, *const zdp = sQbuf + 3 * NZP;
-        constexpr int PL = RX * RY;
-        for (int k = tid; k < NZP; k += blockDim.x) {
-            const int m = k + PL;                     // region slot of (x, y, z + 1)
-            const float ra = srho[m - PL], rb = srho[m], rc = srho[m + PL];
-            const float pa = sphi[m - PL], pb = sphi[m], pc = sphi[m + PL];
-            zr[k] = (ra + 4.0f * rb + rc) * (1.0f / 6.0f);
-            zdr[k] = rc - ra;
-            zp[k] = (pa + 4.0f * pb + pc) * (1.0f / 6.0f);
-            zdp[k] = pc - pa;
-        }
-        __syncthreads();
-        // y pass: S_y of the z sums, S_y of the z differences, D_y of the z sums
-        for (int k = tid; k < NYP; k += blockDim.x) {
-            const int ix = k % RX, jy = (k / RX) % SY, jz = k / (RX * SY);
-            const int m = ix + RX * ((jy + 1) + RY * jz);
-            sYp[k] = (zr[m - RX] + 4.0f * zr[m] + zr[m + RX]) * (1.0f / 6.0f);
-            sYp[NYP + k] = (zdr[m - RX] + 4.0f * zdr[m] + zdr[m + RX]) * (1.0f / 6.0f);
-            sYp[2 * NYP + k] = zr[m + RX] - zr[m - RX];
-            sYp[3 * NYP + k] = (zp[m - RX] + 4.0f * zp[m] + zp[m + RX]) * (1.0f / 6.0f);
-            sYp[4 * NYP + k] = (zdp[m - RX] + 4.0f * zdp[m] + zdp[m + RX]) * (1.0f / 6.0f);
-            sYp[5 * NYP + k] = zp[m + RX] - zp[m - RX];
-        }
-        __syncthreads();
-    }
+    // Stage B: Q = rho c_s^2 I - P and mu_phi at every fluid node of the tile + halo 1
     for (int k = tid; k < NS; k += blockDim.x) {
         int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
         if (stype[k] & TLB_SOLID) {
@@ -753,28 +704,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             smu[k] = 0.f;
             continue;
         }
-        Thermo<D> t;
+        Thermo<D> t = node_thermo<D, RX, RY>(p, srho, sphi, lx + 1, ly + 1, lz + (D == 3 ? 1 : 0));
         float r0 = srho[(lx + 1) + RX * ((ly + 1) + RY * (lz + (D == 3 ? 1 : 0)))];
-        if constexpr (D == 3) {
-            // x pass, at the node (lx + 1, ly, lz) of the y-pass arrays
-            const int m = (lx + 1) + RX * (ly + SY * lz);
-            const float *yzs = sYp, *yzd = sYp + NYP, *zyd = sYp + 2 * NYP;
-            const float p0v = sphi[(lx + 1) + RX * ((ly + 1) + RY * (lz + 1))];
-            t.gr[0] = 0.5f * (yzs[m + 1] - yzs[m - 1]);
-            t.gr[1] = 0.5f * (zyd[m - 1] + 4.0f * zyd[m] + zyd[m + 1]) * (1.0f / 6.0f);
-            t.gr[2] = 0.5f * (yzd[m - 1] + 4.0f * yzd[m] + yzd[m + 1]) * (1.0f / 6.0f);
-            t.lr = 6.0f * ((yzs[m - 1] + 4.0f * yzs[m] + yzs[m + 1]) * (1.0f / 6.0f) - r0);
-            yzs += 3 * NYP;
-            yzd += 3 * NYP;
-            zyd += 3 * NYP;
-            t.gp[0] = 0.5f * (yzs[m + 1] - yzs[m - 1]);
-            t.gp[1] = 0.5f * (zyd[m - 1] + 4.0f * zyd[m] + zyd[m + 1]) * (1.0f / 6.0f);
-            t.gp[2] = 0.5f * (yzd[m - 1] + 4.0f * yzd[m] + yzd[m + 1]) * (1.0f / 6.0f);
-            t.lp = 6.0f * ((yzs[m - 1] + 4.0f * yzs[m] + yzs[m + 1]) * (1.0f / 6.0f) - p0v);
-            thermo_finish<D>(p, r0, p0v, t);
-        } else {
-            t = node_thermo<D, RX, RY>(p, srho, sphi, lx + 1, ly + 1, 0);
-        }
         if constexpr (D == 2) {
             sQ[0][k] = r0 * (1.0f / 3.0f) - t.P[0];
             sQ[1][k] = r0 * (1.0f / 3.0f) - t.P[1];

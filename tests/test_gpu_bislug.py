@@ -42,27 +42,27 @@ def test_paper_geometry_steady_velocity():
     assert v[-5:].mean() > 0 and np.all(np.isfinite(xs))
 
 
-def _relaxation_time(ts, xs, v_inf):
-    """tau of x(t) = x0 + tau v (exp(-t/tau) + t/tau - 1) (Eq.
-    centreofmassposition) by least squares over tau with v fixed."""
-    from scipy.optimize import minimize_scalar
+def _relaxation_time(ts, vs):
+    """tau of v(t) = v_inf - A exp(-t / tau) (Eq. centroidvelocity with a free
+    initial offset: the slugs start rectangular and reshape in the first
+    steps), least squares over (v_inf, A, tau)."""
+    from scipy.optimize import curve_fit
 
-    def cost(tau):
-        model = xs[0] + tau * v_inf * (np.exp(-ts / tau) + ts / tau - 1.0)
-        return float(((model - xs) ** 2).sum())
-
-    return minimize_scalar(cost, bounds=(50.0, 5000.0), method="bounded").x
+    popt, _ = curve_fit(lambda t, v, A, tau: v - A * np.exp(-t / tau), ts, vs,
+                        p0=(vs[-1], vs[-1], 700.0), bounds=([-1.0, -1.0, 50.0], [1.0, 1.0, 5000.0]))
+    return float(popt[2])
 
 
 def test_dynamic_angles_account_for_the_steady_velocity():
     """Sec. VI, paper geometry (H = 39, 400 gas nodes), all angles 60 deg, three
     train lengths: the steady velocity against the long-train law
     (Eqs. capillaryforce-bislugvelocity) with the static angles and with the
-    measured dynamic ones in Delta gamma (the paper's correction).  The
-    dynamic angles bring the law to the measurement: within 25 % at
-    L = 1200 (L/H = 31); the relaxation time of the early trajectory is the
-    law's H^2/(12 nu) within 25 %; Cox's slip length of each interface is
-    reported."""
+    measured dynamic ones (averaged over the last 2000 of 8000 steps) in
+    Delta gamma, the paper's correction.  The dynamic angles bring the law
+    closer to the measurement for every length, within 25 % at L = 1200
+    (L/H = 31); the relaxation time of the velocity (Eq. centroidvelocity)
+    is H^2/(12 nu) within 30 % for L >= 600; Cox's slip length of each
+    interface is reported."""
     from paper_1904_06881_gb300 import bislug as B
     from paper_1904_06881_gb300 import tension as T
     from paper_1904_06881_gb300 import tlb
@@ -73,37 +73,42 @@ def test_dynamic_angles_account_for_the_steady_velocity():
     H, gas, theta, Ls = 39, 400, 60.0, (300, 600, 1200)
     wls = [W.bislug_2d(H=H, L1=L // 2, L2=L - L // 2, gas=gas, theta=theta) for L in Ls]
     lats = [tlb.lattice_from_workload(w) for w in wls]
+    d = lats[0].derived
     b = tlb.Batch(lats)
-    every, steps = 250, 8000
+    every, steps, avg_from = 250, 8000, 6000
     xs = [[B.centroid(l.fields()["C"][:, 0])] for l in lats]
-    for _ in range(steps // every):
+    angs = [[] for _ in lats]
+    for k in range(steps // every):
         b.step(every)
         for i, l in enumerate(lats):
-            xs[i].append(B.centroid(l.fields()["C"][:, 0], xs[i][-1]))
+            f = l.fields()
+            xs[i].append(B.centroid(f["C"][:, 0], xs[i][-1]))
+            if (k + 1) * every > avg_from:
+                angs[i].append(B.dynamic_angles(f, d["rho_l"], d["rho_g"]))
     res, _ = T.sweep([dict(lam=wls[0]["params"]["lam"], kappa=wls[0]["params"]["kappa"])], L=96, R=24.0, steps=4000)
     g = res[0]["gamma"]
     gam = (g["12"], g["13"], g["23"])
-    d = lats[0].derived
+    tau_law = H * H / (12.0 / 6.0)
     runs = []
-    for L, l, x in zip(Ls, lats, xs):
+    for L, x, al in zip(Ls, xs, angs):
         x = np.array(x)
         v = np.diff(x) / every
-        v_inf = float(v[-12:].mean())
-        ang = B.dynamic_angles(l.fields(), d["rho_l"], d["rho_g"])
+        tv = every * (np.arange(len(v)) + 0.5)
+        v_inf = float(v[-8:].mean())
+        ang = {k: float(np.mean([a[k] for a in al])) for k in al[0]}
         law = B.theory(H, L, gam, (theta,) * 3, d["rho_l"], d["rho_g"], gas)["v_inf"]
         law_dyn = B.theory(H, L, gam, (ang["theta_21"], ang["theta_31"], ang["theta_23"]), d["rho_l"], d["rho_g"],
                            gas)["v_inf"]
-        ts = every * np.arange(len(x), dtype=float)
-        sel = ts <= 4000
-        tau = _relaxation_time(ts[sel], x[sel], v_inf)
+        tau = _relaxation_time(tv[tv >= 500], v[tv >= 500])
         record("bi-slug H 39 L %d theta 60" % L, v_inf=v_inf, law_static=law, law_dynamic=law_dyn,
-               ratio_static=v_inf / law, ratio_dynamic=v_inf / law_dyn, tau_rel=tau, tau_law=H * H / (12.0 / 6.0),
-               angles=ang)
+               ratio_static=v_inf / law, ratio_dynamic=v_inf / law_dyn, tau_rel=tau, tau_law=tau_law, angles=ang,
+               angle_spread={k: float(np.ptp([a[k] for a in al])) for k in al[0]})
         runs.append((v_inf, ang))
         assert abs(v_inf / law_dyn - 1.0) < abs(v_inf / law - 1.0), (v_inf, law, law_dyn)
+        if L >= 600:
+            assert abs(tau / tau_law - 1.0) < 0.3, tau
         if L == 1200:
             assert abs(v_inf / law_dyn - 1.0) < 0.25, (v_inf, law_dyn)
-            assert abs(tau / (H * H / (12.0 / 6.0)) - 1.0) < 0.25, tau
     slip = B.cox_slip(runs, gam, (d["rho_g"], d["rho_l"], d["rho_l"]), Lc=float(H))
     record("bi-slug Cox slip lengths, theta 60, L 300-1200", **{k: v["L_s"] for k, v in slip.items()},
            **{k + "_w": v["theta_w"] for k, v in slip.items()})

@@ -38,6 +38,12 @@ def gamma_lg():
 
 @pytest.mark.slow
 def test_laplace_liquid_gas_pairs(gamma_lg):
+    """Laplace's law for the liquid-gas pairs: dP R constant across radii, to
+    3 % between R = 18 and 22 (measured 0.3 %) and 5 % down to R = 14
+    (2.9 %: the interface, about 4 nodes wide, is no longer thin against
+    R); C2 and C3 bubbles alike (set 1 is symmetric)."""
+    g22 = _laplace(22.0, 2, n=80)
+    assert abs(g22 / gamma_lg - 1.0) < 0.03
     g14 = _laplace(14.0, 2)
     assert abs(g14 / gamma_lg - 1.0) < 0.05
     g14_3 = _laplace(14.0, 3)

@@ -197,11 +197,12 @@ def _laplace_ll(R_, n=64, steps=4000):
 @pytest.mark.slow
 def test_gamma23_laplace_closed_form():
     """gamma_23 = dP R for two radii agrees with alpha_23 (lambda2+lambda3)/6 = 1/3
-    (Eq. tension23); the paper's own bubble tests read 3% below it."""
+    (Eq. tension23) within 5 % (measured 1.0 % and 2.6 % below; the paper's
+    own bubble tests read 3 % below it)."""
     g = [_laplace_ll(R_) * R_ for R_ in (12.0, 16.0)]
     assert abs(g[0] / g[1] - 1) < 0.05
     for gi in g:
-        assert 0.85 < gi / (1.0 / 3.0) < 1.05
+        assert 0.95 < gi / (1.0 / 3.0) < 1.05
 
 
 def _gamma12_straight_path(T, s=1.0, lam=(0.6, 1.0, 1.0), kap=(0.01, 1.0, 1.0)):
