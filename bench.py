@@ -47,17 +47,31 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def measured_traffic(workload_name):
-    """DRAM bytes per launch of the step kernel from the committed ncu capture,
-    or None when the kernel sources changed since it was taken."""
+def _counters():
+    """The committed ncu counters of the step kernels (profiles/traffic.json),
+    or {} when the kernel sources changed since they were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             t = json.load(fh)
     except Exception:
-        return None
-    if t.get("source_sha256") != kernel_source_hash():
-        return None
-    return t.get("traffic_bytes_per_launch", {}).get(workload_name)
+        return {}
+    return t if t.get("source_sha256") == kernel_source_hash() else {}
+
+
+def measured_traffic(workload_name):
+    """DRAM bytes per launch of the step kernel from the committed ncu capture,
+    or None when the kernel sources changed since it was taken."""
+    return _counters().get("traffic_bytes_per_launch", {}).get(workload_name)
+
+
+def measured_instructions(workload_name):
+    """Warp instructions executed per launch of the step kernel (ncu
+    smsp__inst_executed.sum), or None as for the traffic."""
+    return _counters().get("warp_instructions_per_launch", {}).get(workload_name)
+
+
+# instruction issue: 4 warp schedulers per SM, one instruction each per cycle
+ISSUE_PER_SM_PER_CLOCK = 4
 
 
 def hbm_peak():
@@ -217,6 +231,20 @@ def measure(lat, stream, steps, warmup, flush=None, kernel_steps=None):
     return step_ms, kern_ms, launches, wall
 
 
+def issue_roofline(workload_name, kern_ms, sm_mhz, n_sm=152):
+    """Instruction issue against the SMs' ceiling (152 SMs x 4 warp
+    instructions per clock at the sampled SM clock): the bound the step
+    kernels meet before HBM, from the committed instruction count."""
+    inst = measured_instructions(workload_name)
+    if not inst or not sm_mhz:
+        return None
+    achieved = inst / (kern_ms * 1e-3) / 1e9
+    peak = n_sm * ISSUE_PER_SM_PER_CLOCK * sm_mhz * 1e6 / 1e9
+    return {"achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "G warp-instructions/s",
+            "frac": round(achieved / peak, 4), "warp_instructions_per_launch": inst,
+            "peak_source": "152 SMs x 4 schedulers x sampled SM clock"}
+
+
 def roofline(Q, N, kern_ms, peak, peak_kind, kernel_name, workload_name):
     achieved = algorithmic_bytes(Q, N) / (kern_ms * 1e-3) / 1e9
     return {"bound": "hbm", "kernel": kernel_name, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -279,6 +307,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "host_wall_s": round(wall, 4),
     }
+    result["roofline"]["issue"] = issue_roofline(wl["name"], kern_ms, result["clocks"].get("sm_mhz"))
     if rank == 0:
         result["e2e"] = e2e_run(wl, tlb)
     if not args.no_large:
