@@ -318,6 +318,8 @@ def c4_requests(seed=4, n=256, rate=20.0, sizes_2d=(64, 128, 256, 512, 1024), si
         th = float(rng.uniform(30.0, THETA_MAX))
         ll = rng.uniform() < 0.125
         ratio = float(np.exp(rng.uniform(np.log(4.0), np.log(ratio_max))))
+        if ll:
+            ratio = ratio_max        # no gas: the EOS of the workloads
         if kind == "drop":
             L = int(rng.choice(sizes_2d))
             mask, rho, phi = sessile_drop_2d(L, L, L / 4.0, xc=L / 2.0, yc=0.5, rho_g=RHO_L / ratio)
