@@ -607,7 +607,14 @@ def run_only(args):
     from paper_1904_06881_gb300 import tlb
     from paper_1904_06881_gb300 import workloads as W
 
-    wl = W.c1_capillary() if args.only == "c1" else workload()
+    if args.only == "c1":
+        wl = W.c1_capillary()
+    elif args.only == "c2_96":
+        # the c2 geometry at 96 x 96 x 128 (0.6 GB on the device, still larger
+        # than L2): the case the detailed ncu captures are taken on
+        wl = W.c2_lubricated(nx=96, ny=96, nz=128, kw_rho=0.02)
+    else:
+        wl = workload()
     stream = torch.cuda.Stream()
     lat = tlb.lattice_from_workload(wl)
     tlb.tlb_set_stream(lat.h, stream.cuda_stream)
@@ -662,7 +669,8 @@ def main():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the reduced-precision run and the large periodic lattices")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the served mix")
-    ap.add_argument("--only", choices=["c1", "c2"], help="time one lattice only (profiling runs): no e2e, no CPU baseline")
+    ap.add_argument("--only", choices=["c1", "c2", "c2_96"],
+                    help="time one lattice only (profiling runs): no e2e, no CPU baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.only:
