@@ -125,3 +125,34 @@ def test_slip_length_recovers_a_planted_slope():
     ths = [math.degrees(brentq(lambda t: B.cox_g(t, lam) - g0 - ca * m, 1e-3, math.pi - 1e-3)) for ca in cas]
     ls, mm = B.slip_length(ths, cas, tw, lam, Lc)
     assert math.isclose(ls, Ls, rel_tol=1e-4) and math.isclose(mm, m, rel_tol=1e-5)
+
+
+def test_cox_slip_recovers_planted_slip_lengths():
+    """cox_slip on angles built from Cox's relation (R25 form) for each
+    interface of a train at three speeds, with a known static angle and slip
+    length per interface, returns them (the static angle as the zero-speed
+    intercept of the angle-speed line, within the line's curvature)."""
+    from scipy.optimize import brentq
+
+    gam = (0.2, 0.21, 0.33)                       # g12, g13, g23
+    rho = (0.43, 6.14, 6.14)                      # gas, C2, C3
+    nu, Lc = 1.0 / 6.0, 39.0
+    planted = {"theta_21": (70.0, 3.0), "theta_23": (75.0, 6.0), "theta_31": (60.0, 2.0)}
+    gmap = {"theta_21": gam[0], "theta_23": gam[2], "theta_31": gam[1]}
+    runs = []
+    for v in (2e-4, 4e-4, 8e-4):
+        ang = {}
+        for key, _, adv, rec in B.INTERFACES:
+            tw, Ls = planted[key]
+            lam = rho[rec] / rho[adv]
+            ca = rho[adv] * nu * v / gmap[key]
+            tw_adv = 180.0 - tw if key == "theta_21" else tw
+            target = B.cox_g(math.radians(tw_adv), lam) + ca * math.log(Lc / Ls)
+            th_adv = math.degrees(brentq(lambda t: B.cox_g(t, lam) - target, 1e-3, math.pi - 1e-3))
+            ang[key] = 180.0 - th_adv if key == "theta_21" else th_adv
+        runs.append((v, ang))
+    out = B.cox_slip(runs, gam, rho, nu=nu, Lc=Lc)
+    for key, (tw, Ls) in planted.items():
+        tw_adv = 180.0 - tw if key == "theta_21" else tw
+        assert abs(out[key]["theta_w"] - tw_adv) < 0.05, (key, out[key])
+        assert abs(out[key]["L_s"] / Ls - 1.0) < 0.05, (key, out[key])
