@@ -305,11 +305,13 @@ enum { TLB_REQ_QUEUED = 0, TLB_REQ_RUNNING = 1, TLB_REQ_DONE = 2, TLB_REQ_FAILED
 
 /* Server with a device-memory budget for resident lattices and a cap on
  * lattices advanced together; steps_per_round steps run between admissions.
- * cuda_stream NULL: the server steps on a stream of its own.  Each pump
- * issues one round of the active lattices through resident batches (one per
- * lattice type and g storage, rebuilt when their members change) and admits
- * queued requests while that round runs on the GPU (their initial fields go
- * through a second stream); requests admitted in a round join the next one. */
+ * cuda_stream NULL: the server steps each group of lattices (lattice type x
+ * g storage) on a stream of its own, so that the groups' rounds overlap on the
+ * GPU; otherwise every group uses cuda_stream.  Each pump issues one round of
+ * the active lattices through resident batches (one per group, rebuilt when
+ * its members change) and admits queued requests while that round runs on
+ * the GPU (their initial fields go through another stream); requests
+ * admitted in a round join the next one. */
 int tlb_server_create(size_t hbm_budget_bytes, int max_active, int steps_per_round, void *cuda_stream,
                       tlb_server **out);
 /* Copy a request in; returns a ticket.  TLB_E_INVAL if the request can never

@@ -1717,7 +1717,10 @@ struct Req {
 struct tlb_server {
     size_t budget;
     int max_active, steps_per_round;
-    cudaStream_t stream;                 // the stepping stream (the caller's, or the server's own)
+    // stepping streams, one per group (lattice type x g storage): the
+    // server's own, so that the groups' rounds overlap on the GPU, or the
+    // caller's stream for all of them
+    cudaStream_t gstream[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t admit = nullptr;        // initial fields of admitted requests
     bool own_stream = false;
     uint64_t next = 1;
@@ -1746,16 +1749,18 @@ extern "C" int tlb_server_create(size_t budget, int max_active, int steps_per_ro
     s->budget = budget;
     s->max_active = max_active;
     s->steps_per_round = steps_per_round;
-    s->stream = (cudaStream_t)stream;
-    if (!s->stream) {
-        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    s->own_stream = stream == nullptr;
+    for (int g = 0; g < 4; ++g) {
+        s->gstream[g] = (cudaStream_t)stream;
+        if (s->own_stream && cudaStreamCreateWithFlags(&s->gstream[g], cudaStreamNonBlocking) != cudaSuccess) {
+            for (int k = 0; k < g; ++k) cudaStreamDestroy(s->gstream[k]);
             delete s;
             return fail(TLB_E_CUDA, "stream creation failed");
         }
-        s->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking) != cudaSuccess) {
-        if (s->own_stream) cudaStreamDestroy(s->stream);
+        if (s->own_stream)
+            for (int g = 0; g < 4; ++g) cudaStreamDestroy(s->gstream[g]);
         delete s;
         return fail(TLB_E_CUDA, "stream creation failed");
     }
@@ -1830,7 +1835,7 @@ static void server_retire_batch(tlb_server *s, int g)
     if (!s->batch[g]) return;
     cudaEvent_t ev = nullptr;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
-        cudaEventRecord(ev, s->stream) == cudaSuccess) {
+        cudaEventRecord(ev, s->gstream[g]) == cudaSuccess) {
         s->retired.push_back({s->batch[g], ev});
     } else {
         if (ev) cudaEventDestroy(ev);
@@ -1839,9 +1844,12 @@ static void server_retire_batch(tlb_server *s, int g)
     s->batch[g] = nullptr;
 }
 
+// group of a lattice: lattice type x g storage (one resident batch each)
+static int server_group(const tlb_params &p) { return (p.lattice == TLB_D3Q27 ? 1 : 0) + (p.g_fp16 ? 2 : 0); }
+
 // one admitted request: context, solid mask and initial fields on the
-// admission stream (the stepping stream keeps running), then the context
-// moves to the stepping stream
+// admission stream (the stepping streams keep running), then the context
+// moves to its group's stepping stream
 static int server_admit_one(tlb_server *s, Req *q)
 {
     int rc = tlb_create_ex(&q->params, &q->ctx);
@@ -1850,7 +1858,7 @@ static int server_admit_one(tlb_server *s, Req *q)
     if ((rc = tlb_set_stream(q->ctx, s->admit))) return rc;
     if (!q->mask.empty() && (rc = tlb_set_solid(q->ctx, q->mask.data()))) return rc;
     if ((rc = tlb_init_fields(q->ctx, q->rho.data(), q->phi.data(), nullptr))) return rc;   // synchronises s->admit
-    return tlb_set_stream(q->ctx, s->stream);
+    return tlb_set_stream(q->ctx, s->gstream[server_group(q->params)]);
 }
 
 extern "C" int tlb_server_pump(tlb_server *s)
@@ -1866,7 +1874,7 @@ extern "C" int tlb_server_pump(tlb_server *s)
         chunk = s->steps_per_round;
         for (Req *q : s->active) chunk = std::min(chunk, q->nsteps - q->done_steps);
         std::vector<tlb_ctx *> groups[4];
-        for (Req *q : s->active) groups[(q->ctx->D == 3 ? 1 : 0) + (q->ctx->p.g_fp16 ? 2 : 0)].push_back(q->ctx);
+        for (Req *q : s->active) groups[server_group(q->ctx->p)].push_back(q->ctx);
         for (int g = 0; g < 4; ++g) {
             if (s->batch[g] && s->batch[g]->ctxs != groups[g]) server_retire_batch(s, g);
             if (groups[g].empty()) continue;
@@ -1899,7 +1907,7 @@ extern "C" int tlb_server_pump(tlb_server *s)
         admitted.push_back(q);
     }
     // 3. retirement of the requests this round completed (their fields are
-    //    read after the round; tlb_get_fields waits for the stepping stream)
+    //    read after the round; tlb_get_fields waits for their group's stream)
     std::vector<Req *> still;
     for (Req *q : s->active) {
         if (q->done_steps >= q->nsteps) {
@@ -1944,7 +1952,7 @@ extern "C" int tlb_server_stats(tlb_server *s, int *queued, int *active, size_t 
 extern "C" void tlb_server_destroy(tlb_server *s)
 {
     if (!s) return;
-    cudaStreamSynchronize(s->stream);
+    for (int g = 0; g < 4; ++g) cudaStreamSynchronize(s->gstream[g]);
     for (int g = 0; g < 4; ++g)
         if (s->batch[g]) tlb_batch_destroy(s->batch[g]);
     server_reap(s, true);
@@ -1952,7 +1960,8 @@ extern "C" void tlb_server_destroy(tlb_server *s)
         if (q->ctx) tlb_destroy(q->ctx);
     for (auto &kv : s->all) delete kv.second;
     if (s->admit) cudaStreamDestroy(s->admit);
-    if (s->own_stream) cudaStreamDestroy(s->stream);
+    if (s->own_stream)
+        for (int g = 0; g < 4; ++g) cudaStreamDestroy(s->gstream[g]);
     delete s;
 }
 

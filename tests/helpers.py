@@ -97,3 +97,37 @@ def match_directions(lattice):
     cg, _ = tlb.tlb_lattice_directions(lattice)
     co, _ = oracle.lattice(lattice)
     return np.array([int(np.where((cg == co[i]).all(1))[0][0]) for i in range(len(co))])
+
+
+def meniscus_fit(rho, half, wall, x_in, x_out):
+    """Meniscus of a liquid column filling a 2D channel (fluid rows wall ..
+    ny - wall - 1, liquid entering at x_in): the rho = half crossing of every
+    row (first one from x_in, linear interpolation), the centre row's crossing
+    relative to x_in, and cos(theta) of the circle through the crossings (a
+    circular meniscus spanning the channel meets the walls at
+    cos(theta) = (H/2)/R).  None when a row has no crossing."""
+    ny = rho.shape[0]
+    ys = np.arange(wall, ny - wall)
+    fx = []
+    for y in ys:
+        row = rho[y]
+        below = np.where(row[x_in:x_out] < half)[0]
+        if len(below) == 0:
+            return None
+        i = x_in + below[0]
+        fx.append(i - 1 + (row[i - 1] - half) / (row[i - 1] - row[i]))
+    fx, yy = np.array(fx), ys.astype(float)
+    A = np.vstack([fx, yy, np.ones_like(fx)]).T
+    Dc, Ec, Fc = np.linalg.lstsq(A, -(fx ** 2 + yy ** 2), rcond=None)[0]
+    R = np.sqrt(Dc ** 2 / 4 + Ec ** 2 / 4 - Fc)
+    return float(fx[len(fx) // 2] - x_in), float(min(1.0, 0.5 * len(ys) / R))
+
+
+def washburn_fit(ts, xs, window=0.1):
+    """Fit x = K sqrt(t - t0) over the last `window` of the samples (least
+    squares on x^2 = K^2 (t - t0)); returns (K, t0)."""
+    ts, xs = np.asarray(ts, float), np.asarray(xs, float)
+    w = slice(int(round((1.0 - window) * len(ts))), len(ts))
+    A = np.vstack([ts[w], np.ones(len(ts[w]))]).T
+    K2, c = np.linalg.lstsq(A, xs[w] ** 2, rcond=None)[0]
+    return float(np.sqrt(K2)), float(-c / K2)

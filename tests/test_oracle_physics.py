@@ -11,9 +11,13 @@ Washburn capillary-filling law (Sec. III bubble test, Sec. V).
   H / (6 nu) (the paper's law when rho_g -> 0).  As in the paper, theta is the
   mean dynamic angle of the meniscus over the analysis window (the second
   half of the run).  Pinned: the rates for theta = 45 and 60 deg scale as
-  their mean cos(theta) (within 5%), and each rate lies within 25% of the
-  prediction (dissipation in the reservoirs and at the diffuse meniscus is
-  left out of the law).
+  their mean cos(theta) (within 5%), and the prefactor K (the square root of
+  the rate ratio: x^2 grows as K^2 t) lies within 10% of the prediction
+  (measured 0.92 and 0.93).  In this short channel (H = 24, x/H of 3 to 5
+  in the window) the flow into the entrance and the diffuse meniscus add
+  friction the law leaves out, a share that falls as the column grows; on
+  the paper's channel (L = 2000, H = 70, run on the GPU library) K agrees
+  within 5%.
 """
 import numpy as np
 import pytest
@@ -92,4 +96,4 @@ def test_washburn_filling_rate(gamma_lg):
     assert abs((r45 / r60) / (c45 / c60) - 1.0) < 0.05
     for rate, c in ((r45, c45), (r60, c60)):
         pred = gamma_lg * c * H / (6.0 * nu)
-        assert 0.75 < rate / pred < 1.05, (rate, pred)
+        assert 0.90 < np.sqrt(rate / pred) < 1.05, (rate, pred)
