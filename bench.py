@@ -476,14 +476,15 @@ def tension_sweep(grid=4, L=96, R=24.0, steps=3000):
                         "theta_deg": [round(v, 2) for v in res[0]["theta"]]}}
 
 
-def _serve(reqs, budget_gb, max_active, steps_per_round, arrivals):
+def _serve(reqs, budget_gb, max_active, steps_per_round, arrivals, policy=0, max_wait_s=0.0):
     """Run the request list through the continuous-batching server: with
     `arrivals` each request is submitted at its Poisson arrival time, else all
     at once (a saturated server).  Time from submission to result per request
     and aggregate MLUPS over the makespan."""
     from paper_1904_06881_gb300 import tlb
 
-    srv = tlb.Server(int(budget_gb * (1 << 30)), max_active=max_active, steps_per_round=steps_per_round)
+    srv = tlb.Server(int(budget_gb * (1 << 30)), max_active=max_active, steps_per_round=steps_per_round,
+                     policy=policy, max_wait_s=max_wait_s)
     t_start = time.perf_counter()
     pending = list(range(len(reqs)))
     tickets, lat, failed = {}, {}, {}
@@ -518,10 +519,12 @@ def _serve(reqs, budget_gb, max_active, steps_per_round, arrivals):
 def served_mix(budget_gb=48.0, max_active=64, steps_per_round=100):
     """The served mix (workloads.c4_requests: 256 requests of drops, channels,
     lubricated substrates, lenses and drop trains, 64^2-1024^2 and 96^3-192^3,
-    liquid-gas and liquid-liquid) through the continuous-batching server,
-    once with Poisson arrivals (20/s) and once with every request submitted
-    at the start (saturated), against the same requests run one after
-    another alone through tlb_step (the same kernels, so the same results)."""
+    liquid-gas and liquid-liquid) through the continuous-batching server:
+    with Poisson arrivals (20/s) admitted in arrival order, the same arrivals
+    admitted least-work first (requests older than 10 s first), and every
+    request submitted at the start (saturated), against the same requests run
+    one after another alone through tlb_step (the same kernels, so the same
+    results)."""
     import torch
 
     from paper_1904_06881_gb300 import tlb
@@ -529,6 +532,8 @@ def served_mix(budget_gb=48.0, max_active=64, steps_per_round=100):
 
     reqs = W.c4_requests()
     poisson, done = _serve(reqs, budget_gb, max_active, steps_per_round, arrivals=True)
+    shortest, _ = _serve(reqs, budget_gb, max_active, steps_per_round, arrivals=True, policy=tlb.SCHED_SHORTEST,
+                         max_wait_s=10.0)
     saturated, _ = _serve(reqs, budget_gb, max_active, steps_per_round, arrivals=False)
     t0 = time.perf_counter()
     for k in done:
@@ -542,9 +547,11 @@ def served_mix(budget_gb=48.0, max_active=64, steps_per_round=100):
     work = poisson["node_steps"]
     return {"workload": "c4 served mix: %d requests (%.1f G node-steps), Poisson 20/s over %.1f s"
                         % (len(reqs), sum(w["nx"] * w["ny"] * w["nz"] * n for _, w, n in reqs) / 1e9, reqs[-1][0]),
-            "poisson": poisson, "saturated": saturated,
+            "poisson": poisson, "poisson_shortest_first": shortest, "saturated": saturated,
             "sequential_alone_mlups": round(work / tseq / 1e6, 1), "sequential_alone_s": round(tseq, 3),
-            "server": {"budget_gb": budget_gb, "max_active": max_active, "steps_per_round": steps_per_round}}
+            "server": {"budget_gb": budget_gb, "max_active": max_active, "steps_per_round": steps_per_round,
+                       "admission": "arrival order; poisson_shortest_first: least work first, requests older "
+                                    "than 10 s first"}}
 
 
 def _cpu_model():

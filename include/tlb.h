@@ -324,6 +324,15 @@ int tlb_server_pump(tlb_server *s);
  * the final fields and the ticket is released. */
 int tlb_poll(tlb_server *s, uint64_t ticket, tlb_result *res, double *rho, double *phi);
 int tlb_server_stats(tlb_server *s, int *queued, int *active, size_t *bytes_in_use);
+/* Admission order (no paper counterpart).  TLB_SCHED_FIFO (the default):
+ * arrival order, the head of the queue waits until its memory is free and
+ * nothing overtakes it.  TLB_SCHED_SHORTEST: the queued request with the least
+ * work (nodes x steps) among those whose memory fits is admitted first (ties
+ * in arrival order); with max_wait_s > 0, requests queued longer than that
+ * come first, in arrival order, and are not overtaken.  Takes effect at the
+ * next pump.  TLB_E_INVAL for an unknown policy or max_wait_s < 0. */
+enum { TLB_SCHED_FIFO = 0, TLB_SCHED_SHORTEST = 1 };
+int tlb_server_set_policy(tlb_server *s, int policy, double max_wait_s);
 void tlb_server_destroy(tlb_server *s);
 
 #ifdef __cplusplus

@@ -1734,6 +1734,8 @@ struct tlb_server {
     // stepping stream has passed the event recorded after their last launch
     tlb_batch *batch[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<std::pair<tlb_batch *, cudaEvent_t>> retired;
+    int policy = TLB_SCHED_FIFO;         // admission order
+    double max_wait_s = 0.0;             // TLB_SCHED_SHORTEST: age after which a request is not overtaken
 };
 
 static size_t footprint(const tlb_params &p)
@@ -1861,6 +1863,40 @@ static int server_admit_one(tlb_server *s, Req *q)
     return tlb_set_stream(q->ctx, s->gstream[server_group(q->params)]);
 }
 
+// work of a request: node updates still to run
+static double req_work(const Req *q)
+{
+    return (double)q->params.nx * q->params.ny * q->params.nz * (double)(q->nsteps - q->done_steps);
+}
+
+// the queued request to admit next: the head (FIFO), or the oldest request
+// past max_wait_s, else the least work among those whose memory fits (the
+// head when none fits, so that the caller stops admitting)
+static std::deque<Req *>::iterator server_pick(tlb_server *s, double now)
+{
+    if (s->policy == TLB_SCHED_FIFO) return s->queue.begin();
+    if (s->max_wait_s > 0.0)
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+            if (now - (*it)->res.submit_s > s->max_wait_s) return it;
+    auto best = s->queue.end();
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if (s->in_use + (*it)->bytes > s->budget) continue;
+        if (best == s->queue.end() || req_work(*it) < req_work(*best)) best = it;
+    }
+    return best == s->queue.end() ? s->queue.begin() : best;
+}
+
+extern "C" int tlb_server_set_policy(tlb_server *s, int policy, double max_wait_s)
+{
+    if (!s) return fail(TLB_E_INVAL, "null server");
+    if ((policy != TLB_SCHED_FIFO && policy != TLB_SCHED_SHORTEST) || !(max_wait_s >= 0.0))
+        return fail(TLB_E_INVAL, "bad policy %d or max_wait_s %g", policy, max_wait_s);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->policy = policy;
+    s->max_wait_s = max_wait_s;
+    return TLB_OK;
+}
+
 extern "C" int tlb_server_pump(tlb_server *s)
 {
     if (!s) return fail(TLB_E_INVAL, "null server");
@@ -1887,14 +1923,15 @@ extern "C" int tlb_server_pump(tlb_server *s)
         }
         for (Req *q : s->active) q->done_steps += chunk;
     }
-    // 2. admission while the round runs: in arrival order while memory and
-    //    slots allow (no overtaking); admitted lattices join the next round
+    // 2. admission while the round runs, in the policy's order while memory
+    //    and slots allow; admitted lattices join the next round
     std::vector<Req *> admitted;
     while (!s->queue.empty() && (int)(s->active.size() + admitted.size()) < s->max_active) {
         NvtxRange admit("tlb_server admit");
-        Req *q = s->queue.front();
+        auto it = server_pick(s, now_s());
+        Req *q = *it;
         if (s->in_use + q->bytes > s->budget) break;
-        s->queue.pop_front();
+        s->queue.erase(it);
         s->in_use += q->bytes;
         q->res.state = TLB_REQ_RUNNING;
         q->res.start_s = now_s();
@@ -1912,6 +1949,9 @@ extern "C" int tlb_server_pump(tlb_server *s)
     for (Req *q : s->active) {
         if (q->done_steps >= q->nsteps) {
             int rc = tlb_sync(q->ctx);
+            // the group's batch refers to this context: retire it before the
+            // context is freed (a context created later may take its address)
+            server_retire_batch(s, server_group(q->ctx->p));
             retire(s, q, rc);
         } else {
             still.push_back(q);

@@ -36,8 +36,9 @@ ENTRY_POINTS = (
     "tlb_device_bytes", "tlb_launch_count", "tlb_step_batch", "tlb_server_create", "tlb_submit",
     "tlb_server_pump", "tlb_poll", "tlb_server_stats", "tlb_server_destroy", "tlb_step_noalloc",
     "tlb_set_force_calibration", "tlb_batch_create", "tlb_batch_step", "tlb_batch_tune", "tlb_batch_get_config",
-    "tlb_batch_destroy", "tlb_derive",
+    "tlb_batch_destroy", "tlb_derive", "tlb_server_set_policy",
 )
+SCHED_FIFO, SCHED_SHORTEST = 0, 1
 ORDER_LATTICE, ORDER_INTERLEAVED, ORDER_LARGEST_FIRST = 0, 1, 2
 
 
@@ -482,13 +483,20 @@ class Batch:
 class Server:
     """Continuous-batching request server (tlb_server_*)."""
 
-    def __init__(self, budget_bytes, max_active=64, steps_per_round=100, stream=None):
+    def __init__(self, budget_bytes, max_active=64, steps_per_round=100, stream=None, policy=SCHED_FIFO,
+                 max_wait_s=0.0):
         h = ctypes.c_void_p()
         _check(lib().tlb_server_create(int(budget_bytes), int(max_active), int(steps_per_round),
                                        ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)),
                "tlb_server_create")
         self.h = h
         self._keep = {}
+        if policy != SCHED_FIFO or max_wait_s:
+            self.set_policy(policy, max_wait_s)
+
+    def set_policy(self, policy, max_wait_s=0.0):
+        _check(lib().tlb_server_set_policy(self.h, int(policy), ctypes.c_double(max_wait_s)),
+               "tlb_server_set_policy")
 
     def submit(self, lattice, nx, ny, nz, mask, rho, phi, nsteps, **kw):
         r = Request()

@@ -159,3 +159,44 @@ def test_batch_follows_lattices_stepped_alone():
     alone[1].step(13)
     for a, m in zip(alone, mix):
         assert _same(a.fields(), m.fields())
+
+
+@pytest.mark.parametrize("policy,max_wait", [("fifo", 0.0), ("shortest", 0.0), ("shortest", 1e-9)])
+def test_server_admission_order(policy, max_wait):
+    """One lattice at a time (max_active = 1): FIFO admits in submission
+    order; TLB_SCHED_SHORTEST admits the least work (nodes x steps) first,
+    unless every request has waited past max_wait_s (then arrival order).
+    Either way each result equals the lattice stepped alone."""
+    from paper_1904_06881_gb300 import tlb
+
+    specs = [(96, 60.0, 200), (48, 80.0, 100), (128, 100.0, 60), (64, 90.0, 300)]
+    reqs = [(W.c3_lattice(dict(L=L, theta=th, wetting=W.WET_GEOM_INTERP)), n) for L, th, n in specs]
+    pol = tlb.SCHED_FIFO if policy == "fifo" else tlb.SCHED_SHORTEST
+    srv = tlb.Server(budget_bytes=256 << 20, max_active=1, steps_per_round=50, policy=pol, max_wait_s=max_wait)
+    tickets = [srv.submit(wl["lattice"], wl["nx"], wl["ny"], wl["nz"], wl["mask"], wl["rho"], wl["phi"], n,
+                          **wl["params"]) for wl, n in reqs]
+    results = {}
+    for _ in range(200):
+        srv.pump()
+        for t in tickets:
+            if t not in results:
+                r = srv.poll(t)
+                if r["state"] in (tlb.REQ_DONE, tlb.REQ_FAILED):
+                    results[t] = r
+        if len(results) == len(tickets):
+            break
+    srv.close()
+    assert len(results) == len(tickets)
+    starts = [results[t]["start_s"] for t in tickets]
+    order = list(np.argsort(starts, kind="stable"))
+    work = [wl["nx"] * wl["ny"] * wl["nz"] * n for wl, n in reqs]
+    if policy == "fifo" or max_wait > 0:
+        assert order == [0, 1, 2, 3]
+    else:
+        assert order == list(np.argsort(work, kind="stable"))
+    for (wl, n), t in zip(reqs, tickets):
+        assert results[t]["state"] == tlb.REQ_DONE
+        a = tlb.lattice_from_workload(wl)
+        a.step(n)
+        assert _same(a.fields(), results[t])
+        a.close()
