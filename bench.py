@@ -406,11 +406,12 @@ def e2e_run(wl, tlb, nsteps=1000, reps=2):
             "job": "tlb_init_fields (host FP64) + %d steps + tlb_get_fields (host FP64)" % nsteps}
 
 
-def batched_sweep(steps=20):
+def batched_sweep(steps=5000, seq_steps=100):
     """The contact-angle sweep (512 D2Q9 lattices, 64^2-512^2, 43.8 M nodes):
-    all lattices advanced by one resident batch (tlb_batch_*: the launch
-    configuration chosen by the autotuner, CUDA-graph replays) against the
-    same lattices advanced one after another by tlb_step."""
+    one sequential pass, every lattice advanced `seq_steps` by tlb_step one
+    after another (steps 3 .. seq_steps + 2), then the whole sweep's `steps`
+    (the configuration's 5000) by one resident batch (tlb_batch_*: the launch
+    configuration chosen by the autotuner, CUDA-graph replays)."""
     import torch
 
     from paper_1904_06881_gb300 import tlb
@@ -425,26 +426,29 @@ def batched_sweep(steps=20):
     t_tune = time.perf_counter() - t0
     batch.step(2)
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for l in lats:
+        l.step(seq_steps)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     batch.step(steps)
     e1.record()
     torch.cuda.synchronize()
     tb = e0.elapsed_time(e1) * 1e-3
+    diverged = 0
     for l in lats:
-        l.step(1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for l in lats:
-        l.step(steps)
-    torch.cuda.synchronize()
-    ts = time.perf_counter() - t0
-    for l in lats:
-        l.sync()
+        try:
+            l.sync()
+        except tlb.TlbError:
+            diverged += 1
     names = {0: "lattice-major", 1: "interleaved", 2: "largest first"}
     res = {"workload": "c3 sweep: %d D2Q9 lattices, %d nodes" % (len(lats), nodes),
-           "batched_mlups": round(nodes * steps / tb / 1e6, 1), "sequential_mlups": round(nodes * steps / ts / 1e6, 1),
-           "speedup": round(ts / tb, 3), "steps": steps,
+           "batched_mlups": round(nodes * steps / tb / 1e6, 1),
+           "sequential_mlups": round(nodes * seq_steps / ts / 1e6, 1),
+           "speedup": round((ts / seq_steps) / (tb / steps), 3), "steps": steps, "sequential_steps": seq_steps,
+           "batched_s": round(tb, 3), "diverged_lattices": diverged,
            "tuned": {"variant": cfg["variant"], "tile_order": names[cfg["tile_order"]],
                      "graph_depth": cfg["graph_depth"], "us_per_step": round(cfg["us_per_step"], 2),
                      "tuning_s": round(t_tune, 3)},

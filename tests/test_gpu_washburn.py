@@ -11,9 +11,11 @@ tension measured by Laplace's law on the same library and <theta> is the mean
 dynamic angle of the meniscus over the window (a circle through the
 rho = (rho_l + rho_g)/2 crossings).
 
-Pinned: K within 5 % of the prediction at theta = 60 and 80 deg (measured
-0.989 and 0.991).  The 60 deg run stops at 1.05 M steps, before the liquid
-reservoir (1024 x 94 nodes) has emptied into the channel.
+Pinned: K within 5 % of the prediction at theta = 60 and 80 deg with
+geometric interpolation (measured 0.989 and 0.991) and at 80 deg with the
+force method, kappa^w from the calibration (measured 0.977: the force method
+deviates more, as the paper reports).  The 60 deg run stops at 1.05 M steps,
+before the liquid reservoir (1024 x 94 nodes) has emptied into the channel.
 """
 import numpy as np
 import pytest
@@ -33,14 +35,19 @@ def gamma_lg():
     return res[0]["gamma"]["12"]
 
 
-@pytest.mark.parametrize("theta,steps", [(60.0, 1050000), (80.0, 1500000)])
-def test_washburn_prefactor_paper_channel(gamma_lg, theta, steps):
+@pytest.mark.parametrize("scheme,theta,steps", [("interpolation", 60.0, 1050000), ("interpolation", 80.0, 1500000),
+                                                ("force", 80.0, 1500000)])
+def test_washburn_prefactor_paper_channel(gamma_lg, scheme, theta, steps):
     from paper_1904_06881_gb300 import tlb
     from paper_1904_06881_gb300 import workloads as W
 
     nx, ny, wall, x_in, x_out, every = 4096, 94, 12, 1024, 3024, 15000
     wl = W.c1_capillary(nx=nx, ny=ny, wall=wall, x_in=x_in, x_out=x_out)
-    wl["params"] = W.base_params(wetting=W.WET_GEOM_INTERP, theta_deg=(theta, 60.0, 120.0))
+    if scheme == "force":
+        # kappa^w from the force-wetting calibration (its D2Q9 range is 75-90 deg)
+        wl["params"] = W.base_params(wetting=W.WET_FORCE, theta_deg=(theta, theta, 90.0))
+    else:
+        wl["params"] = W.base_params(wetting=W.WET_GEOM_INTERP, theta_deg=(theta, 60.0, 120.0))
     lat = tlb.lattice_from_workload(wl)
     d = lat.derived
     half = 0.5 * (d["rho_l"] + d["rho_g"])
@@ -60,7 +67,7 @@ def test_washburn_prefactor_paper_channel(gamma_lg, theta, steps):
     n = len(ts)
     cos_mean = float(np.mean(cs[int(round(0.9 * n)):]))
     K_pred = np.sqrt(gamma_lg * cos_mean * H / (3.0 * NU * d["rho_l"]))
-    record("washburn_paper_channel_%d" % int(theta), K=K, K_pred=K_pred, ratio=K / K_pred,
+    record("washburn_paper_channel_%s_%d" % (scheme, int(theta)), K=K, K_pred=K_pred, ratio=K / K_pred,
            theta_dyn=float(np.degrees(np.arccos(cos_mean))), x_end=xs[-1], gamma=gamma_lg)
     assert xs[-1] > 700.0
     assert abs(K / K_pred - 1.0) < 0.05, (K, K_pred, np.degrees(np.arccos(cos_mean)))
