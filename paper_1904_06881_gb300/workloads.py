@@ -136,10 +136,11 @@ def c2_lubricated(nx=192, ny=192, nz=128, R=32.0, lub=6, gap=4, kw_rho=0.0):
                 nz=nz, params=params, mask=mask, rho=rho, phi=phi, steps=10000)
 
 
-# Largest contact angle drawn for geometric wetting: sessile drops prescribed
-# 135 deg or more leave the FP64 oracle with non-positive populations within
-# 250 steps at this density ratio and resolution (130 deg runs stably).
-THETA_MAX = 130.0
+# Largest contact angle drawn for geometric wetting: a sessile drop of radius
+# L/4 prescribed 129 deg (interpolation) drains the gas at its contact line to
+# non-positive populations within 5000 steps for L >= 256 (within 250 steps in
+# the FP64 oracle at L = 256); 125 deg runs 5000 steps at L = 64 to 512.
+THETA_MAX = 125.0
 
 
 def c3_sweep(seed=3, n=256, sizes=(64, 128, 256, 512)):
@@ -161,10 +162,12 @@ def c3_sweep(seed=3, n=256, sizes=(64, 128, 256, 512)):
 def provisional_kw(theta_deg):
     """Force-method strength for a target angle from a linear fit of sessile
     drops run with the FP64 oracle (radius 16, 64x64: kappa^w = +0.2 gives
-    76 deg, -0.2 gives 102 deg), clipped to |kappa^w| <= 0.3.  Not a
-    calibration: used only to give every force-wetting lattice of a sweep a
-    strength of the right sign and size."""
-    return float(np.clip((90.0 - theta_deg) / 65.0, -0.3, 0.3))
+    76 deg, -0.2 gives 102 deg), clipped to |kappa^w| <= 0.25 (a radius-16
+    drop started as a half disc leaves non-positive populations within 625
+    steps at kappa^w = 0.3, and runs 5000 steps at 0.25).  Not a calibration:
+    used only to give every force-wetting lattice of a sweep a strength of the
+    right sign and size."""
+    return float(np.clip((90.0 - theta_deg) / 65.0, -0.25, 0.25))
 
 
 def c3_lattice(item):
