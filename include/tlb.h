@@ -232,12 +232,12 @@ long long tlb_launch_count(const tlb_ctx *ctx);
  *   On return the advanced populations are in f and g (asynchronously, on
  *   cuda_stream; NULL = legacy default stream).
  * The first call on a device looks up the scratch array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture.  All calls share the one array and it keeps the last
- * call's contents (flags, ghost list and error word are rewritten on every
- * call): calls that overlap on the GPU -- concurrent streams or host threads
- * on one device -- race and must be serialised by the caller.  Divergence is
- * not reported by this call; use a context (tlb_sync) to get it. */
+ * (once per device, with that device current).  All calls share the one
+ * array and it keeps the last call's contents (flags, ghost list and error
+ * word are rewritten on every call): calls that overlap on the GPU --
+ * concurrent streams or host threads on one device -- race and must be
+ * serialised by the caller.  Divergence is not reported by this call; use a
+ * context (tlb_sync) to get it. */
 #define TLB_NOALLOC_MAX_NODES (1 << 20)
 int tlb_step_noalloc(const tlb_params *p, const uint8_t *mask, float *f, float *f_tmp, void *g, void *g_tmp,
                      int nsteps, void *cuda_stream);

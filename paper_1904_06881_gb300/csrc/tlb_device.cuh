@@ -224,13 +224,14 @@ __device__ __forceinline__ float phi_ent(float y, float l)
 //   e4 = (1026 b3 b5 + 540 b4^2 - 702 b6 - 1305 b3^2 b4 + 380 b3^4) / 405,
 //   e5 = (15390 b7 - 23184 b3 b6 - 24570 b4 b5 + 30114 b3^2 b5 + 31080 b3 b4^2
 //         - 36295 b3^3 b4 + 8260 b3^5) / 5670,
-// used as is up to max|x| = 0.07 (against the exact root of random D2Q9 and
-// D3Q27 states its truncation error is below 5e-8 there, and its FP32 value
-// within 2.5e-7, one or two units in the last place of alpha; either moves f
-// by less than 2e-8 of itself) and as the start of Halley's method (third
-// order, from h, h', h''), bracketed by [1, alpha_max), above it (nodes at the
-// interface).
+// used as is up to max|x| = ALPHA_SERIES_MAX = 0.1 (against the exact FP64
+// root of random D2Q9 and D3Q27 states on the equilibrium manifold its
+// truncation error is below 8e-8 at max|x| = 0.07 and 7e-7 at 0.1, about three
+// units in the last place of alpha, and moves f by less than 4e-8 of itself)
+// and as the start of Halley's method (third order, from h, h', h''),
+// bracketed by [1, alpha_max), above it (nodes at the interface).
 // FPA: accessor of f'_i.
+constexpr float ALPHA_SERIES_MAX = 0.1f;
 template <int Q, class FPA>
 __device__ __forceinline__ float alpha_series_a(const FPA &fp, const float (&x)[Q])
 {

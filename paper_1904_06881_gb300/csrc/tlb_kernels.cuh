@@ -949,22 +949,25 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         fp[2 * a + 1] += 0.5f * mF[a];
         fp[2 * a + 2] -= 0.5f * mF[a];
     }
-    // x_i = D_i / f'_i (stored over dl), positivity bound alpha_max = 1 / max(-x_i)
-    float xmax = 0.f, xneg = 0.f;
+    // x_i = D_i / f'_i (stored over dl)
+    float xmax = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         bad |= !(fp[i] > 0.f);
         float xi = dl[i] * (1.0f / fp[i]);
         dl[i] = xi;
         xmax = fmaxf(xmax, fabsf(xi));
-        xneg = fmaxf(xneg, -xi);
     }
     float al = 2.0f;
     if (bad) {
         atomicOr(status, STATUS_DIVERGED);
     } else if (xmax >= 1e-5f) {
         al = alpha_series<Q>(fp, dl);
-        if (xmax > 0.07f) {
+        if (xmax > ALPHA_SERIES_MAX) {
+            // positivity bound alpha_max = 1 / max(-x_i)
+            float xneg = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) xneg = fmaxf(xneg, -dl[i]);
             const float amax = xneg > 0.f ? 1.0f / xneg : 3.0e38f;
             al = alpha_newton<Q>(fp, dl, amax, al);
         }

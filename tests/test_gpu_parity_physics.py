@@ -2,7 +2,7 @@
 the C ABI: contact angles of sessile drops for the three wetting schemes
 (within 0.5 deg), the meniscus track of the capillary channel (within 0.5
 lattice units), and the entropic alpha away from equilibrium, where the CUDA
-path leaves its series root for Halley's method (max_i |x_i| > 0.07,
+path leaves its series root for Halley's method (max_i |x_i| > 0.1,
 x_i = (f^eq_i(u) - f_i) / f'_i; Eqs. EntropyEquation, mirror_state)."""
 import numpy as np
 import pytest
@@ -67,7 +67,7 @@ def test_capillary_meniscus_track_matches_oracle():
 
 def _halley_nodes(o, f, lattice):
     """Fluid nodes whose collision takes Halley's method on the GPU: max_i
-    |x_i| > 0.07, computed on the host from the populations (oracle order)
+    |x_i| > 0.1, computed on the host from the populations (oracle order)
     and the oracle's force of the same state."""
     c, w = oracle.lattice(lattice)
     D = 2 if lattice == W.D2Q9 else 3
@@ -83,7 +83,7 @@ def _halley_nodes(o, f, lattice):
         ue[:D], ud[:D] = u, u + du
         fe, fd = oracle.feq(lattice, rho[n], ue), oracle.feq(lattice, rho[n], ud)
         fp = f[:, n] + fd - fe
-        if np.abs((fe - f[:, n]) / fp).max() > 0.07:
+        if np.abs((fe - f[:, n]) / fp).max() > 0.1:
             idx.append(n)
     return np.array(idx, dtype=np.int64)
 

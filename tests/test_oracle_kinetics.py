@@ -4,8 +4,8 @@
 - product-form equilibrium (Eqs. eqrho, A, B): exact mass and momentum, the
   closed-form second moment of the D1Q3 factor, and that ln(f^eq/w) is linear
   in c (f^eq minimises H at fixed mass and momentum);
-- entropic alpha (Eq. EntropyEquation): residual, bracket and a 50-digit
-  brute-force root;
+- entropic alpha (Eq. EntropyEquation): residual, bracket, a 50-digit
+  brute-force root, and the small-deviation series of the root;
 - g^eq (Sec. II.C): BGK moments phi, phi v, Gamma mu I + phi v v.
 """
 import mpmath
@@ -141,6 +141,56 @@ def test_alpha_tends_to_two_near_equilibrium():
     assert devs[2] < devs[0] and devs[2] < 1e-2
     fp, dl, w = _mirror_and_delta(oracle.D2Q9, rng, 1e-9)
     assert oracle.alpha(oracle.D2Q9, fp, dl) == (2.0, 1)
+
+
+def _series_root(fp, x):
+    """alpha = 2 + e1 + ... + e5: the root of h(alpha) = sum_i f'_i [phi(alpha
+    x_i) - alpha x_i ln(1 + x_i)] expanded in the moments b_k = a_k / a_2,
+    a_k = sum_i f'_i x_i^k, order by order (h(alpha) = sum_k a_k c_k(alpha),
+    c_k = (-1)^k alpha (alpha^(k-1) - k) / (k (k - 1)), a_1 = 0)."""
+    a = {k: float((fp * x ** k).sum()) for k in range(2, 8)}
+    b3, b4, b5, b6, b7 = (a[k] / a[2] for k in range(3, 8))
+    e1 = b3 / 3
+    e2 = 4 * b3 ** 2 / 9 - 2 * b4 / 3
+    e3 = 17 * b3 ** 3 / 27 - 14 * b3 * b4 / 9 + 11 * b5 / 10
+    e4 = 76 * b3 ** 4 / 81 - 29 * b3 ** 2 * b4 / 9 + 38 * b3 * b5 / 15 + 4 * b4 ** 2 / 3 - 26 * b6 / 15
+    e5 = (118 * b3 ** 5 / 81 - 1037 * b3 ** 3 * b4 / 162 + 239 * b3 ** 2 * b5 / 45 + 148 * b3 * b4 ** 2 / 27
+          - 184 * b3 * b6 / 45 - 13 * b4 * b5 / 3 + 19 * b7 / 7)
+    return 2.0 + e1 + e2 + e3 + e4 + e5
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q27])
+def test_alpha_matches_the_small_deviation_series(lat):
+    """Near equilibrium the exact root approaches its asymptotic series: on
+    states f' + D = f^eq(rho, U) with D carrying no mass or momentum and
+    max_i |D_i / f'_i| = m, the oracle's root and the fifth-order series
+    differ by less than 1e-6 at m = 0.1 and 1e-7 at m = 0.07, and the
+    difference falls by at least 4 from m = 0.1 to 0.07 (the sixth-order
+    term scales as m^6: a factor of 8.5)."""
+    c, w = oracle.lattice(lat)
+    Q = len(w)
+    M = np.vstack([np.ones(Q), c[:, 0], c[:, 1], c[:, 2]])
+    P = np.eye(Q) - M.T @ np.linalg.pinv(M.T)
+    rng = np.random.default_rng(11)
+    worst = {}
+    for m in (0.1, 0.07):
+        worst[m] = 0.0
+        for _ in range(200):
+            rho = rng.uniform(0.3, 6.0)
+            U = rng.uniform(-0.1, 0.1, 3)
+            if lat == oracle.D2Q9:
+                U[2] = 0.0
+            fe = oracle.feq(lat, rho, U)
+            d = P @ rng.normal(size=Q)
+            s = m / np.abs(d / fe).max()
+            for _ in range(60):        # scale so that max |d / (fe - d)| = m
+                s *= m / np.abs(s * d / (fe - s * d)).max()
+            d = s * d
+            fp = fe - d
+            al, st = oracle.alpha(lat, fp, d)
+            worst[m] = max(worst[m], abs(al - _series_root(fp, d / fp)))
+    assert worst[0.1] < 1e-6 and worst[0.07] < 1e-7, worst
+    assert worst[0.1] > 4.0 * worst[0.07], worst
 
 
 @pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q27])
