@@ -290,9 +290,11 @@ def run_ours(args):
     cfg.update({"kappa_w": wl["params"]["kw_rho"],
                 "l2": "state 2.1 GB, larger than the 126 MB L2; no flush needed",
                 "parallelism": "replicas" if world > 1 else "single GPU"})
+    fluid = int((wl["mask"] == 0).sum())
     result = {
         "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 5), "higher_is_better": True,
+        "fluid_mlups": round(world * fluid / (step_ms * 1e-3) / 1e6, 2),
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": cfg,
         "roofline": roofline(Q, N, kern_ms, peak, peak_kind,
