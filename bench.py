@@ -626,6 +626,10 @@ def run_only(args):
         # the c2 geometry at 96 x 96 x 128 (0.6 GB on the device, still larger
         # than L2): the case the detailed ncu captures are taken on
         wl = W.c2_lubricated(nx=96, ny=96, nz=128, kw_rho=0.02)
+    elif args.only == "d2q9_2048":
+        # a large periodic D2Q9 lattice at a quarter of the bench's 4096^2
+        # (0.6 GB on the device, larger than L2)
+        wl = W.big_periodic_drop_2d(2048)
     else:
         wl = workload()
     stream = torch.cuda.Stream()
@@ -682,7 +686,7 @@ def main():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the reduced-precision run and the large periodic lattices")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the served mix")
-    ap.add_argument("--only", choices=["c1", "c2", "c2_96"],
+    ap.add_argument("--only", choices=["c1", "c2", "c2_96", "d2q9_2048"],
                     help="time one lattice only (profiling runs): no e2e, no CPU baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
