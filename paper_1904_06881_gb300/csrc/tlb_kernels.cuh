@@ -382,7 +382,7 @@ struct NodesBox {
 // populations itself (no moments pass before the step) and keeps the tile's
 // own populations in shared memory.
 // ---------------------------------------------------------------------------
-template <int D, typename GT, int MODE, bool ASYNC = false, bool FUSED = false>
+template <int D, typename GT, int MODE, bool ASYNC = false, bool FUSED = false, bool FIRSTNB = (D == 3)>
 __device__ __forceinline__ void step_tile(const DevParams &p, const float *__restrict__ f_in, float *__restrict__ f_out,
                                           const void *g_in, void *g_out, const float *__restrict__ rho,
                                           const float *__restrict__ phi, const uint8_t *__restrict__ type,
@@ -975,11 +975,13 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     const float ab = al * local_beta(p, r, ph);
 
     // halfway bounce-back: bit i set when the neighbour x + c_i is solid (one
-    // mask for the f and g stores); D3Q27: only first-layer nodes have solid
-    // neighbours (the D2Q9 kernel, latency-bound, measured faster without
-    // that branch)
+    // mask for the f and g stores).  FIRSTNB: only first-layer nodes have
+    // solid neighbours, so the others skip the test (D3Q27, and the D2Q9
+    // build for launches of more than one wave, which is issue-bound; the
+    // one-wave D2Q9 build is latency-bound and measured faster without the
+    // branch)
     unsigned solid_nb = 0;
-    if (D == 2 || (tc & TLB_FIRST)) {
+    if (!FIRSTNB || (tc & TLB_FIRST)) {
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int m = (sx + cc<D>(i, 0)) + SX * ((sy + cc<D>(i, 1)) + SY * (sz + cc<D>(i, 2)));
@@ -1063,7 +1065,7 @@ __global__ void __launch_bounds__(256, MINB) step_batch_kernel(const BatchEntry 
     __syncthreads();
     AuxOut none = {};
     // D2Q9 tiles sum their own moments; D3Q27 tiles read those of the moments kernel
-    step_tile<D, GT, MODE_STEP, D == 3, D == 2>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type,
+    step_tile<D, GT, MODE_STEP, D == 3, D == 2, (D == 3 || MINB == 4)>(se.p, se.f_in, se.f_out, se.g_in, se.g_out, se.rho, se.phi, se.type,
                                                 se.status, t.y, t.z, t.w, nullptr, none, se.tm);
 }
 
