@@ -57,10 +57,10 @@ struct Tile<3> {
 // periodic wrap of a coordinate at most one period outside [0, n)
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-__device__ __forceinline__ long long node_near(const DevParams &p, int x, int y, int z)
+// (node indices fit in 32 bits: a lattice holds at most 2^31 - 1 nodes)
+__device__ __forceinline__ int node_near(const DevParams &p, int x, int y, int z)
 {
-    return chk_node(
-        (long long)wrap1(x, p.nx) + (long long)p.nx * ((long long)wrap1(y, p.ny) + (long long)p.ny * wrap1(z, p.nz)), p);
+    return (int)chk_node(wrap1(x, p.nx) + p.nx * (wrap1(y, p.ny) + p.ny * wrap1(z, p.nz)), p);
 }
 
 // Programmatic dependent launch: a stepping kernel lets the next one be
@@ -460,7 +460,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         }
         float fa[2][Q], ga[2][Q];
         __half gh[2][Q];                     // FP16 storage: the raw moving populations
-        long long na[2];
+        int na[2];
         bool in[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -603,7 +603,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             const int k = tid + NT * j;
             const int X = x0 - 2 + k % RX, Y = y0 - 2 + (k / RX) % RY, Z = z0 - HZ2 + k / (RX * RY);
             const bool in = k < NR && X < p.nx + 2 && Y < p.ny + 2 && Z < p.nz + 2;
-            const long long n = in ? node_near(p, X, Y, Z) : 0;
+            const int n = in ? node_near(p, X, Y, Z) : 0;
             lt[j] = in ? __ldg(type + n) : (uint8_t)TLB_SOLID;
             lr[j] = in ? __ldg(rho + n) : 0.f;
             lp[j] = in ? __ldg(phi + n) : 0.f;
@@ -743,22 +743,23 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     const int sx = tx + 1, sy = ty + 1, sz = tz + HZ1;
     const int sc = sx + SX * (sy + SY * sz);
     const uint8_t tc = stype[sc];
-    const long long n = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
+    // node indices fit in 32 bits (lattices hold at most 2^31 - 1 nodes)
+    const int n = x + p.nx * (y + p.ny * z);
     if (tc & TLB_SOLID) return;
     // push-streaming store addresses: the node index plus one offset per axis
     // and sign (periodic wrap included), formed once per node
     const int oxm = x == 0 ? p.nx - 1 : -1, oxq = x == p.nx - 1 ? 1 - p.nx : 1;
-    const long long oym = (long long)(y == 0 ? p.ny - 1 : -1) * p.nx;
-    const long long oyq = (long long)(y == p.ny - 1 ? 1 - p.ny : 1) * p.nx;
-    const long long oz = D == 3 ? (long long)p.nx * p.ny : 0;
-    const long long ozm = D == 3 ? (z == 0 ? p.nz - 1 : -1) * oz : 0;
-    const long long ozq = D == 3 ? (z == p.nz - 1 ? 1 - p.nz : 1) * oz : 0;
-    auto nbr = [&](int cx, int cy, int cz) -> long long {
-        long long m = n;
+    const int oym = (y == 0 ? p.ny - 1 : -1) * p.nx;
+    const int oyq = (y == p.ny - 1 ? 1 - p.ny : 1) * p.nx;
+    const int oz = D == 3 ? p.nx * p.ny : 0;
+    const int ozm = D == 3 ? (z == 0 ? p.nz - 1 : -1) * oz : 0;
+    const int ozq = D == 3 ? (z == p.nz - 1 ? 1 - p.nz : 1) * oz : 0;
+    auto nbr = [&](int cx, int cy, int cz) -> int {
+        int m = n;
         if (cx != 0) m += cx > 0 ? oxq : oxm;
         if (cy != 0) m += cy > 0 ? oyq : oym;
         if (D == 3 && cz != 0) m += cz > 0 ? ozq : ozm;
-        return chk_node(m, p);
+        return (int)chk_node(m, p);
     };
     const float r = srho[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
     const float ph = sphi[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
