@@ -588,6 +588,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                 srho[k] = gr;
                 sphi[k] = gp;
             }
+            __syncthreads();      // the ghost values, before stage B reads them
         }
     } else {
         // Stage A: rho, phi and flags of the tile + halo 2, all of a thread's
@@ -683,20 +684,17 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     // for D2Q9 (the loops unroll; measured faster), the run-time one for
     // D3Q27 (the unrolled loops measured 3 % slower)
     const int KSTEP = D == 2 ? NT : (int)blockDim.x;
-    // node flags of the tile + halo 1, from those of the region
+    // Stage B: Q = rho c_s^2 I - P and mu_phi at every fluid node of the tile
+    // + halo 1, with the node flags of the tile + halo 1 (from those of the
+    // region; read by stage C after the barrier that follows)
     for (int k = tid; k < NS; k += KSTEP) {
         const int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
         const int X = x0 - 1 + lx, Y = y0 - 1 + ly, Z = z0 - HZ1 + lz;
-        stype[k] = (X >= p.nx + 1 || Y >= p.ny + 1 || Z >= p.nz + 1)
-                       ? (uint8_t)TLB_SOLID
-                       : srt[(lx + 1) + RX * ((ly + 1) + RY * (lz + (D == 3 ? 1 : 0)))];
-    }
-    __syncthreads();
-
-    // Stage B: Q = rho c_s^2 I - P and mu_phi at every fluid node of the tile + halo 1
-    for (int k = tid; k < NS; k += KSTEP) {
-        int lx = k % SX, ly = (k / SX) % SY, lz = k / (SX * SY);
-        if (stype[k] & TLB_SOLID) {
+        const uint8_t tk = (X >= p.nx + 1 || Y >= p.ny + 1 || Z >= p.nz + 1)
+                               ? (uint8_t)TLB_SOLID
+                               : srt[(lx + 1) + RX * ((ly + 1) + RY * (lz + (D == 3 ? 1 : 0)))];
+        stype[k] = tk;
+        if (tk & TLB_SOLID) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 if constexpr (D == 2) sQ[c][k] = 0.f;
