@@ -126,3 +126,22 @@ def test_derived_constants_match_oracle(L, eos, ratio):
         assert np.isclose(d[k], o[k], rtol=1e-6, atol=0), (k, d[k], o[k])
     for k in ("C", "Psi0"):
         assert np.isclose(d[k], o[k], rtol=1e-5, atol=1e-9), (k, d[k], o[k])
+
+
+def test_committed_counters_match_the_kernel_sources():
+    """The ncu counters in profiles/traffic.json (the bench line's `traffic`
+    and `issue` figures) were taken on the device code as committed: their
+    recorded source hash equals the hash of the current kernel sources, and
+    every workload they cover has a committed summary."""
+    import json
+    import os
+
+    import bench
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "profiles", "traffic.json")) as fh:
+        d = json.load(fh)
+    assert d["source_sha256"] == bench.kernel_source_hash()
+    for name, path in d["captures"].items():
+        assert name in d["traffic_bytes_per_launch"] and name in d["warp_instructions_per_launch"]
+        assert os.path.exists(os.path.join(root, path)), path
