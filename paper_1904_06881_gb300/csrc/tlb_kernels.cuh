@@ -270,13 +270,14 @@ struct Thermo {
 };
 
 template <int D, int RX, int RY>
-__device__ __forceinline__ Thermo<D> node_thermo(const DevParams &p, const float *srho, const float *sphi, int hx,
+__device__ __forceinline__ Thermo<D> node_thermo(const DevParams &p, const float2 *srp, int hx,
                                                  int hy, int hz)
 {
     constexpr int Q = Lat<D>::Q;
     Thermo<D> t;
     int c0 = hx + RX * (hy + RY * hz);
-    float r0 = srho[c0], p0v = sphi[c0];
+    const float2 m0 = srp[c0];
+    float r0 = m0.x, p0v = m0.y;
 #pragma unroll
     for (int a = 0; a < 3; ++a) { t.gr[a] = 0.f; t.gp[a] = 0.f; }
     t.lr = 0.f;
@@ -285,7 +286,8 @@ __device__ __forceinline__ Thermo<D> node_thermo(const DevParams &p, const float
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         int m = (hx + cc<D>(i, 0)) + RX * ((hy + cc<D>(i, 1)) + RY * (hz + cc<D>(i, 2)));
-        float rm = srho[m], pm = sphi[m];
+        const float2 mm = srp[m];
+        float rm = mm.x, pm = mm.y;
         float w3 = 3.0f * wt<D>(i);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
@@ -396,7 +398,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     constexpr int NR = RX * RY * RZ, NS = SX * SY * SZ;
     constexpr int HZ2 = (D == 3) ? 2 : 0, HZ1 = (D == 3) ? 1 : 0;
     constexpr int NC = NQC<D>();
-    __shared__ float srho[NR], sphi[NR];
+    // rho, phi of the tile + halo 2, interleaved (one 8-byte access per node)
+    __shared__ float2 srp[NR];
     // Q = rho c_s^2 I - P of the tile + halo 1: D2Q9 one array per component;
     // D3Q27 per node as {xx, yy, zz, xy} and {xz, yz}, so that the force
     // stencil reads a neighbour's tensor with two vector loads
@@ -518,8 +521,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                     r = 1.0f + r;
                 }
             }
-            srho[kl[s]] = r;
-            sphi[kl[s]] = ph;
+            srp[kl[s]] = make_float2(r, ph);
             srt[kl[s]] = t;
         }
         // Stage A2: the ghost layer of Sec. IV from the fluid moments
@@ -534,8 +536,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                 const int X = x0 - 2 + lx, Y = y0 - 2 + ly;
                 if (X < p.nx + 2 && Y < p.ny + 2) {
                     btyp[kb] = srt[k];
-                    brho[kb] = srho[k];
-                    bphi[kb] = sphi[k];
+                    brho[kb] = srp[k].x;
+                    bphi[kb] = srp[k].y;
                 } else {                      // lattices narrower than a tile
                     const long long n = node_of(p, X, Y, 0);
                     const uint8_t t = __ldg(type + n);
@@ -585,8 +587,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                 const int k = glist[j];
                 float gr, gp;
                 ghost_value<D>(p, acc, x0 - 2 + k % RX, y0 - 2 + k / RX, 0, gr, gp);
-                srho[k] = gr;
-                sphi[k] = gp;
+                srp[k] = make_float2(gr, gp);
             }
             __syncthreads();      // the ghost values, before stage B reads them
         }
@@ -663,8 +664,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             const int k = tid + NT * j;
             if (k >= NR) break;
             srt[k] = lt[j];
-            srho[k] = lr[j];
-            sphi[k] = lp[j];
+            srp[k] = make_float2(lr[j], lp[j]);
             ghost |= (lt[j] & TLB_GHOST) != 0;
         }
         if (ghost) {
@@ -674,8 +674,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
                 if (!(srt[k] & TLB_GHOST)) continue;      // unfilled slots hold TLB_SOLID alone
                 float gr, gp;
                 ghost_value<D>(p, acc, x0 - 2 + k % RX, y0 - 2 + (k / RX) % RY, z0 - HZ2 + k / (RX * RY), gr, gp);
-                srho[k] = gr;
-                sphi[k] = gp;
+                srp[k] = make_float2(gr, gp);
             }
         }
         __syncthreads();
@@ -706,8 +705,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
             smu[k] = 0.f;
             continue;
         }
-        Thermo<D> t = node_thermo<D, RX, RY>(p, srho, sphi, lx + 1, ly + 1, lz + (D == 3 ? 1 : 0));
-        float r0 = srho[(lx + 1) + RX * ((ly + 1) + RY * (lz + (D == 3 ? 1 : 0)))];
+        Thermo<D> t = node_thermo<D, RX, RY>(p, srp, lx + 1, ly + 1, lz + (D == 3 ? 1 : 0));
+        float r0 = srp[(lx + 1) + RX * ((ly + 1) + RY * (lz + (D == 3 ? 1 : 0)))].x;
         if constexpr (D == 2) {
             sQ[0][k] = r0 * (1.0f / 3.0f) - t.P[0];
             sQ[1][k] = r0 * (1.0f / 3.0f) - t.P[1];
@@ -763,8 +762,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
         if (D == 3 && cz != 0) m += cz > 0 ? ozq : ozm;
         return (int)chk_node(m, p);
     };
-    const float r = srho[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
-    const float ph = sphi[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
+    const float2 rph = srp[(sx + 1) + RX * ((sy + 1) + RY * (sz + (D == 3 ? 1 : 0)))];
+    const float r = rph.x, ph = rph.y;
 
     // force F = div(rho c_s^2 I - P) with the wall rules (Sec. IV)
     float F[3] = {0.f, 0.f, 0.f};
@@ -843,7 +842,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const float *__res
     const float mup = smu[sc];
 
     if (MODE == MODE_AUX) {
-        Thermo<D> t = node_thermo<D, RX, RY>(p, srho, sphi, sx + 1, sy + 1, sz + (D == 3 ? 1 : 0));
+        Thermo<D> t = node_thermo<D, RX, RY>(p, srp, sx + 1, sy + 1, sz + (D == 3 ? 1 : 0));
         if (aux.p0) aux.p0[n] = t.b.p0;
         if (aux.mur) aux.mur[n] = t.mur;
         if (aux.mup) aux.mup[n] = t.mup;
