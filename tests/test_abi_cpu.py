@@ -68,6 +68,8 @@ def test_invalid_arguments_rejected_on_host(L):
     with pytest.raises(tlb.TlbError) as e:
         tlb.tlb_create_ex(p)
     assert e.value.code == -4          # geometric angles limited to [20, 160] deg
+    import ctypes
+    assert L.tlb_server_set_policy(None, tlb.SCHED_SHORTEST, ctypes.c_double(0.0)) == -1   # null server
 
 
 @pytest.mark.parametrize("variant", ["check", "timeout_test"])
