@@ -1,0 +1,157 @@
+"""Pins against values the paper prints (fixtures under tests/golden/).
+
+- Table 1: the Neumann angles printed beside each parameter set follow from the
+  printed surface tensions through the oracle's cosine relations (Eqs.
+  theta1fromtension-theta3fromtension), within the printing precision; set 4
+  forms no triangle.  The parameter set the workloads use is set 1.
+- Sec. IV.B, geometric interpolation in 2D: each printed exact case satisfies
+  tan(theta - 90 deg) = offset, and the oracle's ghost (Eq. interp2D) at that
+  angle is the stored value c_{i+offset,k+1} on a field that is not linear.
+- Table 2: the subspace definitions of the surface-tension sweep are the
+  printed ones.
+"""
+import itertools
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.tension as OT
+from paper_1904_06881_gb300 import tension as T
+from paper_1904_06881_gb300 import workloads as W
+
+from test_oracle_thermo import _mk
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+def _table1():
+    out = {}
+    for r in _rows("table1_parameter_sets.txt"):
+        v = [float(x) for x in r[1:]]
+        out[int(r[0])] = dict(lam=tuple(v[0:3]), kappa=tuple(v[3:6]), gamma=tuple(v[6:9]), theta=tuple(v[9:12]))
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_table1_neumann_angles_follow_from_the_printed_tensions(k):
+    """Each printed angle lies inside the range the oracle's Neumann angles
+    take over the box gamma +- 0.0005 (three printed decimals), widened by
+    0.05 deg (one printed decimal).  Over so small a box each angle is
+    monotone in each tension, so the corners bound it.  Set 2 has three
+    different tensions, so an exchanged pair in any relation fails it."""
+    s = _table1()[k]
+    corners = [OT.neumann(*(g + d for g, d in zip(s["gamma"], ds)))
+               for ds in itertools.product((-5e-4, 5e-4), repeat=3)]
+    centre = OT.neumann(*s["gamma"])
+    for j in range(3):
+        lo = min(c[j] for c in corners) - 0.05
+        hi = max(c[j] for c in corners) + 0.05
+        assert lo <= s["theta"][j] <= hi, (k, j, s["theta"][j], centre[j], lo, hi)
+    assert abs(sum(centre) - 360.0) < 1e-9
+
+
+def test_table1_set4_forms_no_triangle():
+    """Set 4 prints no angles: gamma_12 > gamma_13 + gamma_23, so every cosine
+    of the Neumann relations leaves [-1, 1]."""
+    s = _table1()[4]
+    assert all(math.isnan(t) for t in s["theta"])
+    assert all(math.isnan(t) for t in OT.neumann(*s["gamma"]))
+    g12, g13, g23 = s["gamma"]
+    assert g12 > g13 + g23
+
+
+def test_workloads_use_table1_set1():
+    s = _table1()[1]
+    assert W.SET1["lam"] == s["lam"] and W.SET1["kappa"] == s["kappa"]
+    p = W.base_params()
+    assert tuple(p["lam"]) == s["lam"] and tuple(p["kappa"]) == s["kappa"]
+
+
+def _interp_cases():
+    """(printed theta, offset, theta read) for each printed exact case.  The
+    row printed "45" with offset +1 reads 135."""
+    out = []
+    for th, off in _rows("interp2d_exact_cases.txt"):
+        th, off = float(th), int(off)
+        exact = 90.0 + math.degrees(math.atan(off))
+        out.append((th, off, 135.0 if (off == 1 and th == 45.0) else th, exact))
+    return out
+
+
+def test_interp2d_printed_angles_meet_lattice_nodes():
+    """tan(theta - 90 deg) = offset: the printed approximate angles are the
+    exact ones cut to two decimals; the duplicated 45 is the typo for 135."""
+    cases = _interp_cases()
+    assert [c[1] for c in cases] == [-3, -2, -1, 0, 1, 2, 3]
+    for printed, off, read, exact in cases:
+        assert abs(read - exact) < 0.01, (printed, off, exact)
+    typo = [c for c in cases if c[1] == 1][0]
+    assert typo[0] == 45.0 and abs(typo[3] - 135.0) < 1e-12
+
+
+def _wall_row_case(theta):
+    """2D lattice, solid row 0, first fluid row 1.  rho falls along +x in
+    seeded random steps (so the liquid, the phase where rho is high, lies at
+    lower x and the field is not linear); phi = 0 (interface pair 1-2, c =
+    rho, angle theta_21)."""
+    nx, ny = 40, 8
+    o = _mk(nx, ny, wetting=W.WET_GEOM_INTERP, theta_deg=(theta, 70.0, 110.0))
+    d = o.derived
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0, :] = 1
+    o.set_solid(mask)
+    steps = np.random.default_rng(19040).uniform(0.01, 0.05, nx)
+    line = 0.5 * (d["rho_l"] + d["rho_g"]) + 0.5 * steps.sum() - np.cumsum(steps)
+    rho = np.tile(line, (1, ny, 1))
+    o.init_fields(rho, np.zeros_like(rho))
+    return o, line
+
+
+@pytest.mark.parametrize("case", range(7))
+def test_interp2d_exact_cases_take_the_stored_node(case):
+    """At the exact angle the ghost is c_{i+offset,k+1} to rounding; at the
+    printed (cut) angle it is within |l_par - offset| |c_{i+l1} - c_{i+l0}| of
+    it, l_par = tan(theta - 90 deg) (Eq. interp2D)."""
+    printed, off, read, exact = _interp_cases()[case]
+    xs = np.arange(8, 32)
+    o, line = _wall_row_case(exact)
+    g = o.aux("rho_ghost")[0, 0, xs]
+    assert np.abs(g - line[xs + off]).max() < 1e-12, (exact, off)
+    o, line = _wall_row_case(read)
+    g = o.aux("rho_ghost")[0, 0, xs]
+    l_par = math.tan(math.radians(read - 90.0))
+    dmax = np.abs(np.diff(line)).max()
+    assert np.abs(g - line[xs + off]).max() <= abs(l_par - off) * dmax + 1e-12, (read, off)
+    if off != 0:
+        assert np.abs(g - line[xs]).min() > 0.005        # the shift is taken, not a copy
+
+
+def _linear(expr, X, Y):
+    total = 0.0
+    for term in re.findall(r"[+-]?[^+-]+", expr):
+        sign = -1.0 if term.startswith("-") else 1.0
+        term = term.lstrip("+-")
+        if term[-1] in "XY":
+            coef = float(term[:-1]) if term[:-1] else 1.0
+            total += sign * coef * (X if term[-1] == "X" else Y)
+        else:
+            total += sign * float(term)
+    return total
+
+
+@pytest.mark.parametrize("k", range(1, 9))
+def test_table2_subspaces_match_the_sweep(k):
+    row = [r for r in _rows("table2_subspaces.txt") if int(r[0]) == k][0]
+    for X, Y in ((0.3, 0.7), (1.25, 0.45), (0.8, 1.9)):
+        p = T.subspace_params(k, X, Y)
+        want = [_linear(e, X, Y) for e in row[1:]]
+        assert np.allclose(p["lam"] + p["kappa"], want, rtol=0, atol=1e-15), (k, X, Y)
