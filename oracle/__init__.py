@@ -6,11 +6,13 @@ test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package; the CUDA library never does, and the
 two share no code.
 
-Parity pins that constrain each part are in ``tests/test_oracle_*.py``.
+Parity pins that constrain each part are in ``tests/test_oracle_*.py`` and
+``tests/test_golden_cpu.py`` (values the paper prints, ``tests/golden/``).
 Parts with no pin beyond the oracle's own consistency ("parity unpinned"):
-the 3D interpolation support rule (Sec. IV.B, Eq. interp3D: which three of
-four points), the corner/wedge ghost averaging, and the sign convention of
-the force-method strengths kappa_rho^w, kappa_phi^w (Eq. forceBC).
+the tie-break of the 3D interpolation support (Sec. IV.B, Eq. interp3D) when
+two corners lie equally near (i, j), and the weights of the corner/wedge
+ghost average (its mirror symmetry is pinned, which any symmetric
+combination of the single-axis values keeps).
 """
 import ctypes
 import os

@@ -7,6 +7,8 @@
   on a field that is linear along the wall, in 2D and in 3D;
 - the interface-identification rules of Sec. IV.B pick theta_21, theta_31 or
   theta_23;
+- the force method's wall force (Eq. forceBC) on a uniform fluid: -n/6 times
+  the phase's strength, on the second fluid layer only;
 - contact angles: a neutral wall holds 90 deg, geometric angles below and
   above 90 deg spread and bead the drop, the force strength kappa^w > 0
   spreads it.
@@ -55,6 +57,44 @@ def test_uniform_fluid_at_rest_between_walls(lat, wet):
     f = o.fields()
     fl = mask == 0
     assert np.abs(f["rho"][fl] - rl).max() < 1e-12 and np.abs(f["u"]).max() < 1e-14
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q27])
+@pytest.mark.parametrize("phase", ["liquid2", "liquid3", "gas"])
+def test_force_wetting_closed_form(lat, phase):
+    """Eq. forceBC on flat walls with a uniform fluid at rest: the bulk force
+    vanishes (wall rule), and on the second fluid layer alone F_s =
+    rho_rel (kappa_rho^w + phi_rel kappa_phi^w) sum_i w_i s(x + c_i) c_i, where
+    the lattice sum over the first-layer neighbours is -n/6 in D2Q9 and in
+    D3Q27 (n the wall normal into the fluid).  Liquid 2 (phi = chi) takes
+    kappa_rho^w + kappa_phi^w, liquid 3 (phi = -chi) kappa_rho^w -
+    kappa_phi^w, the gas (rho_rel = 0) none."""
+    kr, kp = 0.03, 0.07
+    if lat == oracle.D2Q9:
+        shape, o = (1, 10, 6), _mk(6, 10, wetting=W.WET_FORCE, kw_rho=kr, kw_phi=kp)
+    else:
+        shape, o = (8, 5, 5), _mk(5, 5, 8, lat=lat, wetting=W.WET_FORCE, kw_rho=kr, kw_phi=kp)
+    mask = np.zeros(shape, np.uint8)
+    if lat == oracle.D2Q9:
+        mask[0, 0, :] = mask[0, -1, :] = 1
+    else:
+        mask[0] = mask[-1] = 1
+    o.set_solid(mask)
+    d = o.derived
+    rho, phi, amp = {"liquid2": (d["rho_l"], 5.0, kr + kp), "liquid3": (d["rho_l"], -5.0, kr - kp),
+                     "gas": (d["rho_g"], 0.0, 0.0)}[phase]
+    o.init_fields(np.full(shape, rho), np.full(shape, phi))
+    axis = "Fy" if lat == oracle.D2Q9 else "Fz"
+    Fn = o.aux(axis)
+    Fn = Fn[0] if lat == oracle.D2Q9 else Fn          # wall-normal axis first
+    layers = Fn.reshape(Fn.shape[0], -1)
+    want = np.zeros(layers.shape[0])
+    want[2], want[-3] = -amp / 6.0, amp / 6.0        # second layer above the lower and below the upper wall
+    fl = slice(1, layers.shape[0] - 1)
+    assert np.abs(layers[fl] - want[fl, None]).max() < 1e-13, (phase, layers[:, 0])
+    for k in ("Fx", "Fy", "Fz"):
+        if k != axis:
+            assert np.abs(o.aux(k)[mask == 0]).max() < 1e-13
 
 
 def _ghost_case_2d(wet, theta, slope, rho_mid=None, phi_of=None, nx=40):
@@ -130,6 +170,69 @@ def test_ghost_linear_field_3d(wet, theta, direction):
     sl = (slice(6, 18), slice(6, 18))
     expect = rho[1][sl] + s / np.tan(np.radians(theta))
     assert np.abs(g[sl] - expect).max() < 1e-12
+
+
+@pytest.mark.parametrize("corner", [(2, 0), (3, 0), (2, 1), (3, 1)])
+def test_interp3d_support_drops_the_nearest_corner(corner):
+    """Eq. interp3D takes the plane through the three of the four corners of
+    the cell holding (l_x, l_y) that lie furthest from (i, j).  At cot(theta) =
+    2.5 along the unit direction (0.985, 0.171), (l_x, l_y) = (2.46, 0.43) lies
+    in the cell [2, 3] x [0, 1], whose corner nearest (i, j) is (2, 0).  A spike
+    on the first fluid layer at that corner leaves the ghost at (i, j) on the
+    linear field's value; a spike at a kept corner moves it by its barycentric
+    weight in the triangle (3, 0), (2, 1), (3, 1).  The spikes sit two or more
+    nodes from (i, j), outside the in-plane gradient's stencil."""
+    n, nz, s, spike = 24, 6, 0.04, 0.3
+    theta = np.degrees(np.arctan(1.0 / 2.5))
+    o = _mk(n, n, nz, lat=oracle.D3Q27, wetting=W.WET_GEOM_INTERP, theta_deg=(theta, 70.0, 110.0))
+    d = o.derived
+    rl, rg = d["rho_l"], d["rho_g"]
+    mask = np.zeros((nz, n, n), np.uint8)
+    mask[0] = mask[-1] = 1            # the ghost at z = 0 then faces fluid on one side only
+    o.set_solid(mask)
+    u = np.array([0.92, 0.16]) / np.hypot(0.92, 0.16)
+    z, y, x = np.mgrid[0:nz, 0:n, 0:n].astype(float)
+    rho = 0.5 * (rl + rg) + s * (u[0] * (x - n / 2) + u[1] * (y - n / 2))
+    i, j = 8, 10
+    rho[1, j + corner[1], i + corner[0]] += spike
+    phi = 5.0 * (rho - rg) / (rl - rg)
+    o.init_fields(rho, phi)
+    g = o.aux("rho_ghost")[0, j, i]
+    linear = 0.5 * (rl + rg) + s * (u[0] * (i - n / 2) + u[1] * (j - n / 2)) + s * 2.5
+    lx, ly = 2.5 * u
+    b = 3.0 - lx                      # weight of (2, 1): x = 3 a + 2 b + 3 c with a + b + c = 1
+    c = ly - b                        # weight of (3, 1): y = b + c
+    weight = {(2, 0): 0.0, (3, 0): 1.0 - b - c, (2, 1): b, (3, 1): c}[corner]
+    assert abs(g - (linear + weight * spike)) < 1e-12, (corner, g - linear, weight * spike)
+
+
+@pytest.mark.parametrize("wet", [W.WET_GEOM_EXTRAP, W.WET_GEOM_INTERP])
+def test_corner_ghosts_keep_the_diagonal_mirror_symmetry(wet):
+    """A solid square block in a periodic box, a drop centred on the
+    diagonal: the problem is symmetric under x <-> y, which maps a corner
+    ghost's two fluid-facing axes onto each other.  Averaging the single-axis
+    ghost values over the fluid-facing axes keeps the symmetry, at the block's
+    off-diagonal corners too (taking either axis alone breaks it there), and
+    the step keeps it: the fields stay mirror-symmetric to rounding over 200
+    steps."""
+    n = 32
+    o = _mk(n, n, wetting=wet, theta_deg=(60.0, 70.0, 110.0))
+    mask = np.zeros((1, n, n), np.uint8)
+    mask[0, 12:18, 12:18] = 1
+    o.set_solid(mask)
+    yy, xx = np.mgrid[0:n, 0:n].astype(float)
+    C2 = 0.5 * (1 - np.tanh((np.hypot(xx - 10.0, yy - 10.0) - 6.0) / 2.0))
+    rho, phi = W.phase_fields(C2, np.zeros_like(C2))
+    rho, phi = rho.reshape(1, n, n), phi.reshape(1, n, n)
+    o.init_fields(rho, phi)
+    g = o.aux("rho_ghost")[0]
+    ring = mask[0].astype(bool)
+    assert np.abs(g - g.T)[ring].max() < 1e-13
+    # the two single-axis values differ at the off-diagonal corners, so the rule is exercised there
+    assert abs(g[12, 17] - rho[0, 12, 18]) > 1e-4 and abs(g[12, 17] - rho[0, 11, 17]) > 1e-4
+    o.step(200)
+    r = o.fields()["rho"][0]
+    assert np.abs(r - r.T).max() < 1e-10
 
 
 def _contact_angle(rho, rl, rg, wall_plane=0.5):
