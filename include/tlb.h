@@ -233,8 +233,12 @@ long long tlb_launch_count(const tlb_ctx *ctx);
  *   cuda_stream; NULL = legacy default stream).
  * The first call on a device looks up the scratch array's device address
  * (once per device, with that device current).  All calls share the one
- * array and it keeps the last call's contents (flags, ghost list and error
- * word are rewritten on every call): calls that overlap on the GPU --
+ * array and it keeps the last call's contents.  The error word is reset on
+ * every call.  The node flags and ghost list are built from the mask on the
+ * host and uploaded when the lattice, the sizes, the mask's contents or the
+ * stream differ from the previous call's on this device; otherwise the copy
+ * in the array is used again (one N-byte comparison instead of the host pass
+ * over the mask and its upload).  Calls that overlap on the GPU --
  * concurrent streams or host threads on one device -- race and must be
  * serialised by the caller.  Divergence is not reported by this call; use a
  * context (tlb_sync) to get it. */

@@ -2018,6 +2018,12 @@ namespace {
 struct NoallocDevice {
     bool ready = false;
     unsigned char *base = nullptr;    // device address of g_noalloc_scratch
+    // the geometry whose node flags and ghost list the array holds, and the
+    // stream that uploaded them (later work on that stream sees the upload)
+    bool have_geom = false;
+    int lattice = -1, nx = 0, ny = 0, nz = 0, nghost = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<uint8_t> mask;        // empty: no walls
 };
 std::mutex g_noalloc_mu;
 NoallocDevice g_noalloc_dev[64];
@@ -2045,21 +2051,18 @@ extern "C" int tlb_step_noalloc(const tlb_params *pin, const uint8_t *mask, floa
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(TLB_E_UNSUPPORTED, "device index %d out of range", dev);
-    unsigned char *base;
-    {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoallocDevice &nd = g_noalloc_dev[dev];
+    if (!nd.ready) {
         // set-up once per device, with that device current: the device address
         // of the scratch array (its host-side name is not a device address)
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        NoallocDevice &nd = g_noalloc_dev[dev];
-        if (!nd.ready) {
-            void *ptr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess) return fail(TLB_E_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            nd.base = (unsigned char *)ptr;
-            nd.ready = true;
-        }
-        base = nd.base;
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return fail(TLB_E_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        nd.base = (unsigned char *)ptr;
+        nd.ready = true;
     }
+    unsigned char *base = nd.base;
     // derived constants: host computation only
     static thread_local tlb_params last_p;
     static thread_local tlb_derived last_d;
@@ -2073,11 +2076,7 @@ extern "C" int tlb_step_noalloc(const tlb_params *pin, const uint8_t *mask, floa
         have_last = true;
     }
     DevParams dp = make_dev(*p, last_d);
-    // node flags and ghost list from the host mask (the rules of tlb_set_solid)
     int D = Dof(p->lattice);
-    std::vector<uint8_t> flags;
-    std::vector<int> ghosts;
-    node_flags(p->nx, p->ny, p->nz, D, mask, flags, ghosts);
     size_t M = TLB_NOALLOC_MAX_NODES;
     DevState s;
     s.rho = (float *)base;
@@ -2085,16 +2084,39 @@ extern "C" int tlb_step_noalloc(const tlb_params *pin, const uint8_t *mask, floa
     s.ghosts = (int *)(base + M * 8);
     s.type = (uint8_t *)(base + M * 12);
     s.status = (unsigned *)(base + M * 13);
-    s.nghost = (int)ghosts.size();
     s.f[0] = f;
     s.f[1] = f_tmp;
     s.g[0] = g;
     s.g[1] = g_tmp;
     s.cur = 0;
-    // the array keeps the previous call's contents: reset what must start fresh
-    CUDA_TRY(cudaMemcpyAsync(s.type, flags.data(), (size_t)N, cudaMemcpyHostToDevice, st));
-    if (!ghosts.empty())
-        CUDA_TRY(cudaMemcpyAsync(s.ghosts, ghosts.data(), ghosts.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    // Node flags and ghost list from the host mask (the rules of
+    // tlb_set_solid).  The array keeps them from the previous call on this
+    // device: when the lattice, the sizes, the mask and the stream are the
+    // same, that copy is used again and the host pass over the mask skipped
+    // (the kernels only read it).  Any other call rebuilds and uploads them.
+    bool same = nd.have_geom && nd.lattice == p->lattice && nd.nx == p->nx && nd.ny == p->ny &&
+                nd.nz == p->nz && nd.stream == st && (mask == nullptr) == nd.mask.empty() &&
+                (mask == nullptr || std::memcmp(mask, nd.mask.data(), (size_t)N) == 0);
+    if (!same) {
+        nd.have_geom = false;
+        std::vector<uint8_t> flags;
+        std::vector<int> ghosts;
+        node_flags(p->nx, p->ny, p->nz, D, mask, flags, ghosts);
+        CUDA_TRY(cudaMemcpyAsync(s.type, flags.data(), (size_t)N, cudaMemcpyHostToDevice, st));
+        if (!ghosts.empty())
+            CUDA_TRY(cudaMemcpyAsync(s.ghosts, ghosts.data(), ghosts.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                     st));
+        nd.lattice = p->lattice;
+        nd.nx = p->nx;
+        nd.ny = p->ny;
+        nd.nz = p->nz;
+        nd.stream = st;
+        nd.nghost = (int)ghosts.size();
+        if (mask) nd.mask.assign(mask, mask + N);
+        else nd.mask.clear();
+        nd.have_geom = true;
+    }
+    s.nghost = nd.nghost;
     CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(unsigned), st));
     AuxOut none = {};
     for (int k = 0; k < nsteps; ++k) {

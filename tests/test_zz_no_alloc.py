@@ -7,8 +7,9 @@ pool that a raw cudaMalloc would bypass, a loop that cannot take the
 synchronisation an allocation may imply); its scratch is a static device
 array inside the library.  The cases cover geometric wetting (D2Q9 channel),
 force wetting given by contact angles only, whose strengths come from the
-registered calibration tables exactly as for a context, and a small D3Q27
-lattice.
+registered calibration tables exactly as for a context, a small D3Q27
+lattice, and two masks in turn (the node flags and ghost list kept from the
+previous call are reused only for the same geometry).
 
 This file is named to be collected last, so that a run stopping at the first
 failure has run every other test before it.
@@ -79,6 +80,46 @@ def test_step_noalloc_d3q27():
     wl = W.c2_lubricated(nx=24, ny=20, nz=20, R=5.0, lub=3, gap=2)
     wl["params"] = W.base_params(wetting=W.WET_FORCE, theta_deg=(90.0, th, 90.0))
     _compare(wl, 3)
+
+
+def test_step_noalloc_reuses_and_rebuilds_the_geometry():
+    """Two lattices of the same type and size whose masks differ (a wall
+    below; walls below and above), stepped in the order A, B, A, A on one
+    stream: the node flags and ghost list are reused for the repeated A and
+    rebuilt at each change of mask, and every call matches its context."""
+    import torch
+
+    from paper_1904_06881_gb300 import tlb
+
+    nx, ny = 64, 48
+    mask_a, rho, phi = W.sessile_drop_2d(nx, ny, 14.0, xc=30.3, yc=0.5, walls=("bottom",))
+    mask_b = mask_a.copy()
+    mask_b[..., ny - 1, :] = 1
+    params = W.base_params(wetting=W.WET_GEOM_INTERP, theta_deg=(60.0, 60.0, 120.0))
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    state = {}
+    for name, mask in (("A", mask_a), ("B", mask_b)):
+        wl = dict(lattice=W.D2Q9, nx=nx, ny=ny, nz=1, mask=mask, rho=rho, phi=phi, params=params)
+        ref = tlb.lattice_from_workload(wl)
+        c, w = tlb.tlb_lattice_directions(W.D2Q9)
+        f0, g0 = ref.populations()
+        f = torch.tensor((f0 - w[:, None]).astype(np.float32), device=dev)
+        g = torch.tensor(g0.astype(np.float32), device=dev)
+        state[name] = (wl, ref, w, f, g, torch.empty_like(f), torch.empty_like(g))
+    p = tlb.make_params(W.D2Q9, nx, ny, 1, **params)
+    for name in ("A", "B", "A", "A"):
+        wl, ref, w, f, g, f_tmp, g_tmp = state[name]
+        tlb.tlb_step_noalloc(p, wl["mask"], f.data_ptr(), f_tmp.data_ptr(), g.data_ptr(), g_tmp.data_ptr(), 4,
+                             stream)
+        ref.step(4)
+        torch.cuda.synchronize()
+        fr, gr = ref.populations()
+        fl = wl["mask"].reshape(-1) == 0
+        fn = f.double().cpu().numpy() + w[:, None]
+        gn = g.double().cpu().numpy()
+        assert np.abs(fn[:, fl] - fr[:, fl]).max() <= 3e-6 * np.abs(fr[:, fl]).max(), name
+        assert np.abs(gn[:, fl] - gr[:, fl]).max() <= 3e-6 * np.abs(gr[:, fl]).max(), name
 
 
 def test_step_noalloc_rejects_oversize_lattice():
