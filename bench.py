@@ -642,6 +642,65 @@ def run_only(args):
             "note": "profiling run; not a benchmark line"}
 
 
+def run_noalloc(args):
+    """The allocation-free entry point (tlb_step_noalloc: moments, ghost and
+    step launches per step) against a context's fused step on the same
+    lattice, the D2Q9 1024x64 capillary channel (65,536 nodes, L2-resident
+    for both), device time per step by CUDA events on one stream; and the host
+    time of one call when the previous call left the same geometry."""
+    import torch
+
+    from paper_1904_06881_gb300 import tlb
+    from paper_1904_06881_gb300 import workloads as W
+
+    wl = W.c1_capillary()
+    stream = torch.cuda.Stream()
+    lat = tlb.lattice_from_workload(wl)
+    tlb.tlb_set_stream(lat.h, stream.cuda_stream)
+    c, w = tlb.tlb_lattice_directions(wl["lattice"])
+    f0, g0 = lat.populations()
+    dev = torch.device("cuda")
+    f = torch.tensor((f0 - w[:, None]).astype(np.float32), device=dev)
+    g = torch.tensor(g0.astype(np.float32), device=dev)
+    f_tmp, g_tmp = torch.empty_like(f), torch.empty_like(g)
+    p = tlb.make_params(wl["lattice"], wl["nx"], wl["ny"], wl["nz"], **wl["params"])
+    K = 2 * max(1, (args.steps + 1) // 2)          # even: the result ends in f, g without a copy
+
+    def noalloc(n):
+        tlb.tlb_step_noalloc(p, wl["mask"], f.data_ptr(), f_tmp.data_ptr(), g.data_ptr(), g_tmp.data_ptr(), n,
+                             stream.cuda_stream)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(K)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    noalloc(2 * args.warmup)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    na_ms = min(timed(noalloc) for _ in range(3))
+    ctx_ms = min(timed(lat.step) for _ in range(3))
+    torch.cuda.synchronize()
+    calls = 50
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        noalloc(2)
+    host_us = (time.perf_counter() - t0) / calls * 1e6
+    torch.cuda.synchronize()
+    lat.close()
+    N = wl["nx"] * wl["ny"] * wl["nz"]
+    return {"workload": wl["name"], "steps_per_timing": K,
+            "noalloc": {"ms_per_step": round(na_ms, 5), "MLUPS": round(N / (na_ms * 1e-3) / 1e6, 1),
+                        "launches_per_step": 3},
+            "context": {"ms_per_step": round(ctx_ms, 5), "MLUPS": round(N / (ctx_ms * 1e-3) / 1e6, 1)},
+            "noalloc_host_us_per_call_2_steps": round(host_us, 1),
+            "note": "entry-point comparison; not a benchmark line"}
+
+
 def run_reference(args):
     """The oracle (the reference arm: the paper has no code) on the host cores,
     on the headline workload's bounded sample: one oracle time step of a
@@ -686,11 +745,13 @@ def main():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the reduced-precision run and the large periodic lattices")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep and the served mix")
-    ap.add_argument("--only", choices=["c1", "c2", "c2_96", "d2q9_2048"],
+    ap.add_argument("--only", choices=["c1", "c2", "c2_96", "d2q9_2048", "noalloc"],
                     help="time one lattice only (profiling runs): no e2e, no CPU baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.only:
+    if args.only == "noalloc":
+        res = run_noalloc(args)
+    elif args.only:
         res = run_only(args)
     else:
         res = run_reference(args) if args.impl == "reference" else run_ours(args)
