@@ -1,9 +1,10 @@
 """Physics pins of the oracle: Laplace's law for the liquid-gas pairs and the
 Washburn capillary-filling law (Sec. III bubble test, Sec. V).
 
-- Laplace: a 2D drop in gas has dP = gamma / R; dP R agrees for R = 14 and 18
-  within 5%, and a liquid-2 and a liquid-3 drop give the same gamma (set 1 is
-  symmetric in the two liquids: gamma_12 = gamma_13).
+- Laplace: a 2D drop in gas has dP = gamma / R; dP R agrees for R = 18 and 22
+  within 3% and down to R = 14 within 5%, and a liquid-2 and a liquid-3 drop
+  give the same gamma (set 1 is symmetric in the two liquids: gamma_12 =
+  gamma_13).
 - Washburn (Eqs. capforce, viscousforce, Washburn, Washburnprefactor): the
   capillary force 2 gamma cos(theta) balances Poiseuille friction.  At this
   density ratio (14) the gas column ahead of the meniscus also dissipates, so
