@@ -215,10 +215,11 @@ long long tlb_launch_count(const tlb_ctx *ctx);
  * owns a fixed device-memory budget carved up in advance, hosts whose
  * allocator is a framework pool that raw cudaMalloc would bypass, and loops
  * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
- * imply.  tlb_step_noalloc advances caller-owned populations by nsteps and
- * allocates nothing: its scratch (moments, node flags, ghost list, error
- * word) is one static device array of TLB_NOALLOC_MAX_NODES * 13 + 256 bytes
- * (13.6 MB) that every GPU loading this library holds until exit.
+ * imply.  tlb_step_noalloc advances caller-owned populations by nsteps with
+ * the kernels of tlb_step (the same populations, bit for bit) and allocates
+ * nothing: its scratch (moments, tile table, node flags, error word, the two
+ * batch entries) is one static device array of TLB_NOALLOC_MAX_NODES * 25 +
+ * 1280 bytes (26.2 MB) that every GPU loading this library holds until exit.
  *   p          lattice, sizes and physics; at most TLB_NOALLOC_MAX_NODES
  *              (1048576) nodes, else TLB_E_INVAL; g_fp16 must be 0.  Force
  *              wetting given by angles takes its strengths from the
@@ -233,9 +234,10 @@ long long tlb_launch_count(const tlb_ctx *ctx);
  *   cuda_stream; NULL = legacy default stream).
  * The first call on a device looks up the scratch array's device address
  * (once per device, with that device current).  All calls share the one
- * array and it keeps the last call's contents.  The error word is reset on
- * every call.  The node flags and ghost list are built from the mask on the
- * host and uploaded when the lattice, the sizes, the mask's contents or the
+ * array and it keeps the last call's contents.  Every call resets the error
+ * word and rewrites the batch entries (they hold f, g and their work
+ * buffers).  The node flags and the tile table are built on the host and
+ * uploaded when the lattice, the sizes, the mask's contents or the
  * stream differ from the previous call's on this device; otherwise the copy
  * in the array is used again (one N-byte comparison instead of the host pass
  * over the mask and its upload).  Calls that overlap on the GPU --

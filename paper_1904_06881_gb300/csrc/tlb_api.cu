@@ -2007,12 +2007,22 @@ extern "C" void tlb_server_destroy(tlb_server *s)
 
 // ---------------------------------------------------------------------------
 // Allocation-free stepping for callers that cannot allocate device memory
-// (no paper counterpart).  The moments, ghost list, node flags and error word
+// (no paper counterpart).  The step runs the kernels of tlb_step (the batch
+// kernels over a table of one lattice's tiles); their moments, tile table,
+// node flags, error word and the two batch entries (one per buffer parity)
 // live in one file-scope device array, so the call performs no cudaMalloc,
 // cudaFree or other allocation on the device.
 // ---------------------------------------------------------------------------
-// layout: rho (N floats) | phi (N floats) | ghost list (N ints) | flags (N bytes) | status word
-static __device__ __align__(256) unsigned char g_noalloc_scratch[(size_t)TLB_NOALLOC_MAX_NODES * 13 + 256];
+// layout, M = TLB_NOALLOC_MAX_NODES: rho (M floats) | phi (M floats) |
+// tiles (M int4: a tile holds at least one node) | flags (M bytes) |
+// status word (256 bytes reserved) | entries (2 BatchEntry, 1024 bytes reserved)
+constexpr size_t NOALLOC_M = TLB_NOALLOC_MAX_NODES;
+constexpr size_t NOALLOC_PHI = NOALLOC_M * 4, NOALLOC_TILES = NOALLOC_M * 8, NOALLOC_FLAGS = NOALLOC_M * 24,
+                 NOALLOC_STATUS = NOALLOC_M * 25, NOALLOC_ENTRIES = NOALLOC_M * 25 + 256,
+                 NOALLOC_BYTES = NOALLOC_M * 25 + 256 + 1024;
+static_assert(2 * sizeof(BatchEntry) <= 1024, "batch entries exceed their reserved bytes");
+static_assert(NOALLOC_TILES % 16 == 0 && NOALLOC_ENTRIES % 256 == 0, "scratch alignment");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 namespace {
 struct NoallocDevice {
@@ -2021,7 +2031,7 @@ struct NoallocDevice {
     // the geometry whose node flags and ghost list the array holds, and the
     // stream that uploaded them (later work on that stream sees the upload)
     bool have_geom = false;
-    int lattice = -1, nx = 0, ny = 0, nz = 0, nghost = 0;
+    int lattice = -1, nx = 0, ny = 0, nz = 0, ntiles = 0;
     cudaStream_t stream = nullptr;
     std::vector<uint8_t> mask;        // empty: no walls
 };
@@ -2077,23 +2087,17 @@ extern "C" int tlb_step_noalloc(const tlb_params *pin, const uint8_t *mask, floa
     }
     DevParams dp = make_dev(*p, last_d);
     int D = Dof(p->lattice);
-    size_t M = TLB_NOALLOC_MAX_NODES;
-    DevState s;
-    s.rho = (float *)base;
-    s.phi = (float *)(base + M * 4);
-    s.ghosts = (int *)(base + M * 8);
-    s.type = (uint8_t *)(base + M * 12);
-    s.status = (unsigned *)(base + M * 13);
-    s.f[0] = f;
-    s.f[1] = f_tmp;
-    s.g[0] = g;
-    s.g[1] = g_tmp;
-    s.cur = 0;
-    // Node flags and ghost list from the host mask (the rules of
-    // tlb_set_solid).  The array keeps them from the previous call on this
-    // device: when the lattice, the sizes, the mask and the stream are the
-    // same, that copy is used again and the host pass over the mask skipped
-    // (the kernels only read it).  Any other call rebuilds and uploads them.
+    float *rho = (float *)base;
+    float *phi = (float *)(base + NOALLOC_PHI);
+    int4 *tiles = (int4 *)(base + NOALLOC_TILES);
+    uint8_t *type = base + NOALLOC_FLAGS;
+    unsigned *status = (unsigned *)(base + NOALLOC_STATUS);
+    BatchEntry *entries = (BatchEntry *)(base + NOALLOC_ENTRIES);
+    // Node flags (the rules of tlb_set_solid) and the tile table of the
+    // lattice.  The array keeps them from the previous call on this device:
+    // when the lattice, the sizes, the mask and the stream are the same, that
+    // copy is used again and the host pass over the mask skipped (the kernels
+    // only read it).  Any other call rebuilds and uploads them.
     bool same = nd.have_geom && nd.lattice == p->lattice && nd.nx == p->nx && nd.ny == p->ny &&
                 nd.nz == p->nz && nd.stream == st && (mask == nullptr) == nd.mask.empty() &&
                 (mask == nullptr || std::memcmp(mask, nd.mask.data(), (size_t)N) == 0);
@@ -2102,36 +2106,57 @@ extern "C" int tlb_step_noalloc(const tlb_params *pin, const uint8_t *mask, floa
         std::vector<uint8_t> flags;
         std::vector<int> ghosts;
         node_flags(p->nx, p->ny, p->nz, D, mask, flags, ghosts);
-        CUDA_TRY(cudaMemcpyAsync(s.type, flags.data(), (size_t)N, cudaMemcpyHostToDevice, st));
-        if (!ghosts.empty())
-            CUDA_TRY(cudaMemcpyAsync(s.ghosts, ghosts.data(), ghosts.size() * sizeof(int), cudaMemcpyHostToDevice,
-                                     st));
+        int TX = D == 2 ? Launch<2>::tile_dims(0) : Launch<3>::tile_dims(0);
+        int TY = D == 2 ? Launch<2>::tile_dims(1) : Launch<3>::tile_dims(1);
+        int TZ = D == 2 ? Launch<2>::tile_dims(2) : Launch<3>::tile_dims(2);
+        std::vector<int4> tl;
+        for (int z = 0; z < p->nz; z += TZ)
+            for (int y = 0; y < p->ny; y += TY)
+                for (int x = 0; x < p->nx; x += TX) tl.push_back(make_int4(0, x, y, z));
+        if (tl.size() > NOALLOC_M) return fail(TLB_E_INVAL, "tile table exceeds the scratch array");
+        CUDA_TRY(cudaMemcpyAsync(type, flags.data(), (size_t)N, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(tiles, tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
         nd.lattice = p->lattice;
         nd.nx = p->nx;
         nd.ny = p->ny;
         nd.nz = p->nz;
         nd.stream = st;
-        nd.nghost = (int)ghosts.size();
+        nd.ntiles = (int)tl.size();
         if (mask) nd.mask.assign(mask, mask + N);
         else nd.mask.clear();
         nd.have_geom = true;
     }
-    s.nghost = nd.nghost;
-    CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(unsigned), st));
-    AuxOut none = {};
+    // one batch entry per buffer parity: parity 0 reads f, g and writes
+    // f_tmp, g_tmp; parity 1 the other way round (no tensor maps: the step
+    // kernel copies a tile's own populations with cp.async)
+    BatchEntry ent[2];
+    for (int par = 0; par < 2; ++par) {
+        ent[par] = BatchEntry{};
+        ent[par].p = dp;
+        ent[par].f_in = par ? f_tmp : f;
+        ent[par].f_out = par ? f : f_tmp;
+        ent[par].g_in = par ? g_tmp : g;
+        ent[par].g_out = par ? g : g_tmp;
+        ent[par].rho = rho;
+        ent[par].phi = phi;
+        ent[par].type = type;
+        ent[par].status = status;
+        for (int k = 0; k < 3; ++k) ent[par].tm[k] = nullptr;
+    }
+    CUDA_TRY(cudaMemcpyAsync(entries, ent, sizeof(ent), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
+    const int ntiles = nd.ntiles;
+    int cur = 0;
     for (int k = 0; k < nsteps; ++k) {
         if (D == 2) {
-            Launch<2>::moments(dp, s, st);
-            Launch<2>::ghosts(dp, s, st);
-            Launch<2>::step(dp, s, MODE_STEP, nullptr, none, st);
+            Launch<2>::step_batch(entries + cur, tiles, ntiles, 0, st);
         } else {
-            Launch<3>::moments(dp, s, st);
-            Launch<3>::ghosts(dp, s, st);
-            Launch<3>::step(dp, s, MODE_STEP, nullptr, none, st);
+            Launch<3>::moments_batch(entries + cur, tiles, ntiles, 0, st);
+            Launch<3>::step_batch(entries + cur, tiles, ntiles, 0, st);
         }
-        s.cur ^= 1;
+        cur ^= 1;
     }
-    if (s.cur == 1) {
+    if (cur == 1) {
         size_t QN = (size_t)Qof(p->lattice) * (size_t)N;
         CUDA_TRY(cudaMemcpyAsync(f, f_tmp, QN * 4, cudaMemcpyDeviceToDevice, st));
         CUDA_TRY(cudaMemcpyAsync(g, g_tmp, QN * 4, cudaMemcpyDeviceToDevice, st));
