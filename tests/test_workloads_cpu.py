@@ -1,5 +1,8 @@
 """The seeded synthetic inputs (workloads.py) follow their stated recipes.
 
+- c0 (the D2Q9 sessile drop with its seeded noise), c1 (the capillary
+  channel) and c2 (the bench's headline D3Q27 lubricated substrate): sizes,
+  walls, phases and wetting parameters.
 - c3, the batched contact-angle sweep: 256 draws of L in {64, 128, 256, 512}
   and theta_21 ~ U[30, THETA_MAX], each run with force and with geometric-
   interpolation wetting (512 lattices); a sessile drop of radius L/4 on the
@@ -99,3 +102,70 @@ def test_c4_request_mix_recipe():
     assert 0.04 < n_ll / n_2d < 0.25, (n_ll, n_2d)
     again = W.c4_requests(sizes_3d=(24, 32))
     assert [(r[0], r[1]["name"], r[2]) for r in again] == [(r[0], r[1]["name"], r[2]) for r in reqs]
+
+
+def _concentrations(wl):
+    """C1, C2, C3 from (rho, phi) by the inverse of workloads.phase_fields."""
+    p = wl["params"]
+    C1 = (wl["rho"] - p["rho_l"]) / (p["rho_g"] - p["rho_l"])
+    d = wl["phi"] / p["chi"]                      # C2 - C3
+    return C1, 0.5 * (1.0 - C1 + d), 0.5 * (1.0 - C1 - d)
+
+
+def test_c0_recipe():
+    """D2Q9 64x64, walls at rows 0 and 63, a liquid-1 cap of radius 16 on the
+    bottom wall, U[-1e-3, 1e-3] noise on C2 and C3, force wetting with
+    kappa^w = 0; the noise is the seed's."""
+    wl = W.c0_sessile_drop()
+    assert (wl["nx"], wl["ny"], wl["nz"], wl["lattice"]) == (64, 64, 1, W.D2Q9)
+    m = wl["mask"].reshape(64, 64)
+    assert m[0].all() and m[63].all() and not m[1:63].any()
+    C1, C2, C3 = (c.reshape(64, 64) for c in _concentrations(wl))
+    area = C2[1:63].sum()
+    assert abs(area / (0.5 * np.pi * 16.0 ** 2) - 1.0) < 0.05, area
+    gas = C1[40:63] > 0.99                        # far above the cap
+    assert gas.sum() > 1000
+    assert np.abs(C3[40:63][gas]).max() <= 1e-3 + 1e-12 and np.abs(C3[40:63][gas]).max() > 5e-4
+    assert np.abs(C2[40:63][gas]).max() <= 1e-3 + 1e-12
+    p = wl["params"]
+    assert p["wetting"] == W.WET_FORCE and p["kw_rho"] == 0.0 and p["kw_phi"] == 0.0
+    assert np.array_equal(W.c0_sessile_drop()["rho"], wl["rho"])
+    assert not np.array_equal(W.c0_sessile_drop(seed=1)["rho"], wl["rho"])
+
+
+def test_c1_recipe():
+    """D2Q9 1024x64: solid slabs y < 12 and y >= 52 for x in [256, 960) leave a
+    channel of height 40; liquid 1 fills x < 256 at full height, gas the rest;
+    geometric interpolation with 30/60/120 deg."""
+    wl = W.c1_capillary()
+    assert (wl["nx"], wl["ny"], wl["lattice"]) == (1024, 64, W.D2Q9)
+    m = wl["mask"].reshape(64, 1024)
+    y, x = np.mgrid[0:64, 0:1024]
+    want = (x >= 256) & (x < 960) & ((y < 12) | (y >= 52))
+    assert np.array_equal(m.astype(bool), want)
+    assert wl["channel"]["H"] == 40
+    C1, C2, C3 = (c.reshape(64, 1024) for c in _concentrations(wl))
+    assert C2[:, 20:236].min() > 0.99 and C1[:, 300:940].min() > 0.99
+    assert np.abs(C3).max() < 1e-12
+    p = wl["params"]
+    assert p["wetting"] == W.WET_GEOM_INTERP and tuple(p["theta_deg"]) == (30.0, 60.0, 120.0)
+
+
+def test_c2_headline_recipe():
+    """The bench's headline lattice: D3Q27 192x192x128, walls at z = 0 and 127,
+    a liquid-2 film z in [1, 6], a liquid-1 sphere of radius 32 whose bottom
+    lies 4 nodes above the film, force wetting with kappa_rho^w = 0.02."""
+    import bench
+
+    wl = bench.workload()
+    assert (wl["nx"], wl["ny"], wl["nz"], wl["lattice"]) == (192, 192, 128, W.D3Q27)
+    m = wl["mask"]
+    assert m[0].all() and m[127].all() and not m[1:127].any()
+    C1, C2, C3 = _concentrations(wl)
+    # the film, away from the drop: its tanh edge (width 2) puts C3 = 1/2 at z = 6.5
+    assert C3[1, 10, 10] > 0.99 and C3[6, 10, 10] > 0.5 > C3[7, 10, 10] and C2[3, 10, 10] < 1e-6
+    assert C1[60, 10, 10] > 0.99                                 # gas above the film
+    assert C2[42, 96, 96] > 0.99                                 # the sphere's centre, z = 6 + 4 + 32
+    assert abs(C2[10, 96, 96] - 0.5) < 0.05                     # its bottom, 4 nodes above the film
+    p = wl["params"]
+    assert p["wetting"] == W.WET_FORCE and p["kw_rho"] == 0.02
