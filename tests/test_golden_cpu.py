@@ -125,6 +125,23 @@ def test_subspace4_gamma23_follows_the_closed_form(X, Y):
     assert o.fields()["C"][0].max() < 0.02
 
 
+@pytest.mark.slow
+def test_subspace4_liquid_gas_tensions_follow_their_own_liquid():
+    """Sec. III on subspace 4: gamma_12 depends mainly on X = lambda_2 and
+    gamma_13 on Y = lambda_3.  The oracle's bubbles (64^2, R = 16, 4000
+    steps): doubling X raises gamma_12 from 0.124 to 0.227 and doubling Y
+    moves it by 4e-4; exchanging the liquids (X <-> Y, C2 <-> C3) maps
+    gamma_12 onto gamma_13 (set 1's phi -> -phi symmetry, here with kappa_2 !=
+    kappa_3)."""
+    def g(pair, X, Y):
+        return OT.laplace(OT.bubble(pair, 64, 16.0, 4000, **T.subspace_params(4, X, Y)), pair)
+
+    g0, gx, gy = g("12", 0.6, 0.6), g("12", 1.2, 0.6), g("12", 0.6, 1.2)
+    assert gx - g0 > 0.5 * g0
+    assert abs(gy - g0) < 0.02 * (gx - g0)
+    assert abs(g("13", 1.2, 0.6) / gy - 1.0) < 1e-6
+
+
 def test_workloads_use_table1_set1():
     s = _table1()[1]
     assert W.SET1["lam"] == s["lam"] and W.SET1["kappa"] == s["kappa"]
